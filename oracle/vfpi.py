@@ -1,0 +1,229 @@
+"""Plain FP64 V-FPI (Alg. 1 with Alg. 2), written out in the paper's order.
+
+Test infrastructure only (see the package docstring).
+
+Notation follows the paper: ``A v = b + J_c^T lambda_c`` (eq. lindyn), nodal
+contact Jacobian rows ``J_{c,m} = [.. R_m .. -R_m ..]`` (eq. jcnode, the ``-R``
+block only for a D-contact), diagonal step matrix ``W``, surrogate step
+``v* = v - W (A v - b)`` (eq. pgd1), surrogate contact problem
+``lambda_c = SOL(eta_c, Gamma_c)`` with ``Gamma_c = J_c W J_c^T`` and
+``eta_c = J_c v*`` (eq. subp), one-shot solve (Alg. 2, eq. operator) and update
+``v^{l+1} = v* + W J_c^T lambda_c`` (eq. vup).  The residual
+``theta = ||v^{l+1} - v^l||`` and the stop test follow Alg. 1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+STRICT = "strict"
+PROXIMAL = "proximal"
+NORM_ABS = "abs"      # theta = ||dv||_2 (Alg. 1)
+NORM_RMS = "rms"      # theta = ||dv||_2 / sqrt(n)
+
+
+@dataclasses.dataclass
+class Problem:
+    """The data of one V-FPI problem, promoted to float64."""
+
+    A: sp.spmatrix            # n x n, SPD
+    b: np.ndarray             # [n]
+    node_i: np.ndarray        # [n_c]
+    node_j: np.ndarray        # [n_c], -1 for an S-contact
+    R: np.ndarray             # [n_c, 3, 3], rows n, t1, t2
+    mu: np.ndarray            # [n_c]
+    phi: np.ndarray           # [n_c]
+    Jc: sp.spmatrix           # 3 n_c x n, eq. (jcnode)
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def n_c(self) -> int:
+        return self.node_i.shape[0]
+
+
+def make_problem(row_ptr, col_idx, vals, b, node_i, node_j, R, mu, phi) -> Problem:
+    """Assemble ``A`` (BSR, 3x3 blocks) and ``J_c`` (eq. jcnode) in float64."""
+    vals = np.asarray(vals, dtype=np.float64).reshape(-1, 3, 3)
+    N = len(row_ptr) - 1
+    A = sp.bsr_matrix((vals, np.asarray(col_idx), np.asarray(row_ptr)), shape=(3 * N, 3 * N))
+    node_i = np.asarray(node_i, dtype=np.int64)
+    node_j = np.asarray(node_j, dtype=np.int64)
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3, 3)
+    n_c = node_i.shape[0]
+    rows, cols, data = [], [], []
+    for sign, nodes, keep in ((1.0, node_i, np.ones(n_c, bool)), (-1.0, node_j, node_j >= 0)):
+        m = np.nonzero(keep)[0]
+        r = 3 * m[:, None, None] + np.arange(3)[None, :, None]
+        c = 3 * nodes[m][:, None, None] + np.arange(3)[None, None, :]
+        rows.append(np.broadcast_to(r, (len(m), 3, 3)).ravel())
+        cols.append(np.broadcast_to(c, (len(m), 3, 3)).ravel())
+        data.append((sign * R[m]).ravel())
+    Jc = sp.csr_matrix((np.concatenate(data), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(3 * n_c, 3 * N))
+    return Problem(A=A, b=np.asarray(b, dtype=np.float64).copy(), node_i=node_i, node_j=node_j,
+                   R=R, mu=np.asarray(mu, dtype=np.float64).copy(),
+                   phi=np.asarray(phi, dtype=np.float64).copy(), Jc=Jc)
+
+
+# ----------------------------------------------------------------------------
+# Choice of W (Sec. IV.C)
+# ----------------------------------------------------------------------------
+
+def frobenius_w(P: Problem) -> np.ndarray:
+    """Diagonal W minimising ``||I - W A||_F`` under the tying of Prop. 3.
+
+    Row by row, ``||I - W A||_F^2 = sum_r (1 - 2 w_r a_rr + w_r^2 ||A_r*||^2)``,
+    so a group of DOFs sharing one value ``w`` takes
+    ``w = sum a_rr / sum ||A_r*||^2`` (Sec. IV.C; the three DOFs of a node in
+    contact form one group, the six DOFs of a D-contact's two nodes form one
+    group) and every other DOF takes ``w_rr = a_rr / ||A_r*||^2``.
+    """
+    A = P.A.tocsr()
+    d = A.diagonal().astype(np.float64)
+    s = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    w = d / s
+    for m in range(P.n_c):
+        nodes = [P.node_i[m]] + ([P.node_j[m]] if P.node_j[m] >= 0 else [])
+        dofs = np.concatenate([np.arange(3 * q, 3 * q + 3) for q in nodes])
+        w[dofs] = d[dofs].sum() / s[dofs].sum()
+    return w
+
+
+def scalar_w(P: Problem, alpha: float) -> np.ndarray:
+    """``W = alpha I`` (Sec. IV.C)."""
+    return np.full(P.n, float(alpha))
+
+
+def optimal_alpha(P: Problem) -> float:
+    """``alpha = 2 / (sigma_min(A) + sigma_max(A))`` (Sec. IV.C), dense eigenvalues."""
+    ev = np.linalg.eigvalsh(P.A.toarray())
+    return 2.0 / (ev[0] + ev[-1])
+
+
+# ----------------------------------------------------------------------------
+# ProjectFC (eq. operator)
+# ----------------------------------------------------------------------------
+
+def project_strict(lam_star: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """Strict operator: ``lambda_n = max(lambda*_n, 0)``, then the tangential part
+    is projected onto the disk of radius ``mu lambda_n`` (the cross-section of the
+    friction cone at ``lambda_n``)."""
+    lam_star = np.asarray(lam_star, dtype=np.float64).reshape(-1, 3)
+    lam = np.empty_like(lam_star)
+    lam[:, 0] = np.maximum(lam_star[:, 0], 0.0)
+    t = lam_star[:, 1:]
+    rho = np.sqrt(t[:, 0] ** 2 + t[:, 1] ** 2)
+    radius = mu * lam[:, 0]
+    inside = rho <= radius
+    scale = np.where(inside, 1.0, radius / np.where(inside, 1.0, rho))
+    lam[:, 1:] = t * scale[:, None]
+    return lam
+
+
+def project_proximal(lam_star: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """Proximal operator: Euclidean projection onto the cone
+    ``{lambda_n >= 0, ||lambda_t|| <= mu lambda_n}`` (eq. operator, eq. genfc)."""
+    lam_star = np.asarray(lam_star, dtype=np.float64).reshape(-1, 3)
+    a = lam_star[:, 0]
+    t = lam_star[:, 1:]
+    r = np.sqrt(t[:, 0] ** 2 + t[:, 1] ** 2)
+    lam = np.zeros_like(lam_star)
+    inside = r <= mu * a
+    polar = mu * r <= -a
+    edge = ~inside & ~polar
+    lam[inside] = lam_star[inside]
+    ln = (a[edge] + mu[edge] * r[edge]) / (1.0 + mu[edge] ** 2)
+    lam[edge, 0] = ln
+    lam[edge, 1:] = (mu[edge] * ln / r[edge])[:, None] * t[edge]
+    return lam
+
+
+# ----------------------------------------------------------------------------
+# One sweep and the loop (Alg. 1, Alg. 2)
+# ----------------------------------------------------------------------------
+
+def gamma_blocks(P: Problem, w: np.ndarray) -> np.ndarray:
+    """Diagonal 3x3 blocks ``Gamma_{c,m} = J_{c,m} W J_{c,m}^T`` of eq. (subp)."""
+    G = np.zeros((P.n_c, 3, 3))
+    for sign_nodes in (P.node_i, P.node_j):
+        m = np.nonzero(sign_nodes >= 0)[0]
+        Wn = w.reshape(-1, 3)[sign_nodes[m]]                   # [k, 3]
+        G[m] += np.einsum("kab,kb,kcb->kac", P.R[m], Wn, P.R[m])
+    return G
+
+
+@dataclasses.dataclass
+class SweepResult:
+    v_next: np.ndarray
+    v_star: np.ndarray
+    eta: np.ndarray           # [n_c, 3]
+    lam_star: np.ndarray      # [n_c, 3]
+    lam: np.ndarray           # [n_c, 3]
+    theta: float
+
+
+def sweep(P: Problem, w: np.ndarray, v: np.ndarray, operator: str = STRICT,
+          norm: str = NORM_ABS, omega: np.ndarray | None = None) -> SweepResult:
+    """One V-FPI iteration from ``v = v^l``.
+
+    ``omega`` (optional, [n_c, 3, 3]) is added to ``Gamma_c`` as in the
+    invertible-contact extension (eq. invt).
+    """
+    v = np.asarray(v, dtype=np.float64)
+    # eq. (pgd1): gradient / surrogate-splitting step
+    v_star = v - w * (P.A @ v - P.b)
+    # eq. (subp): eta_c = J_c v*, Gamma_c = J_c W J_c^T (block diagonal, Prop. 3)
+    eta = (P.Jc @ v_star).reshape(-1, 3)
+    Gam = gamma_blocks(P, w)
+    if omega is not None:
+        Gam = Gam + omega
+    # Alg. 2: lambda*_m = -Gamma_m^{-1} (eta_m + phi_m), phi_m = [phi_n; 0; 0]
+    rhs = eta.copy()
+    rhs[:, 0] += P.phi
+    lam_star = -np.linalg.solve(Gam, rhs[:, :, None])[:, :, 0] if P.n_c else rhs
+    lam = (project_strict if operator == STRICT else project_proximal)(lam_star, P.mu)
+    # eq. (vup): v^{l+1} = v* + W J_c^T lambda_c
+    v_next = v_star + w * (P.Jc.T @ lam.ravel())
+    dv = v_next - v
+    theta = math.sqrt(math.fsum(dv * dv))
+    if norm == NORM_RMS:
+        theta /= math.sqrt(P.n)
+    return SweepResult(v_next, v_star, eta, lam_star, lam, theta)
+
+
+@dataclasses.dataclass
+class SolveResult:
+    v: np.ndarray
+    lam: np.ndarray
+    lam_star: np.ndarray
+    iters: int
+    theta: float
+    converged: bool
+    thetas: list
+
+
+def solve(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, l_max: int,
+          operator: str = STRICT, norm: str = NORM_ABS, omega=None) -> SolveResult:
+    """Alg. 1 inner loop: sweep, residual, break on ``theta < theta_th`` or ``l = l_max``."""
+    v = np.asarray(v0, dtype=np.float64).copy()
+    thetas = []
+    l = 1
+    while True:
+        r = sweep(P, w, v, operator, norm, omega)
+        thetas.append(r.theta)
+        if r.theta < theta_th or l == l_max:
+            break
+        v = r.v_next
+        l += 1
+    return SolveResult(r.v_next, r.lam, r.lam_star, l, r.theta, r.theta < theta_th, thetas)
+
+
+def integrate(x: np.ndarray, v: np.ndarray, h: float) -> np.ndarray:
+    """State update ``x_{k+1} = x_k + h v_hat`` (eq. disc_dyn, backward-Euler reading)."""
+    return np.asarray(x, dtype=np.float64) + h * np.asarray(v, dtype=np.float64)

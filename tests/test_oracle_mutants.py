@@ -1,0 +1,94 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the pins
+catch every one of them.
+
+Each mutant rewrites one line of an oracle function's source (a flipped sign,
+a dropped term, a transposed operand, a wrong index) and re-executes it in the
+oracle module's namespace; the pin suite of ``test_oracle_pins`` must then
+fail.  A replacement that does not match the current source fails the test
+too, so a mutant can never silently become a no-op.
+"""
+import inspect
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle.vfpi as ov
+import oracle.adjoint as oadj
+from tests import test_oracle_pins as pins
+
+MUTANTS = {
+    "scatter_sign": (ov, "sweep", "v_next = v_star + w * (P.Jc.T @", "v_next = v_star - w * (P.Jc.T @"),
+    "dropped_phi": (ov, "sweep", "rhs[:, 0] += P.phi", "rhs[:, 0] += 0.0 * P.phi"),
+    "gradient_sign": (ov, "sweep", "v_star = v - w * (P.A @ v - P.b)", "v_star = v - w * (P.A @ v + P.b)"),
+    "eta_from_v": (ov, "sweep", "eta = (P.Jc @ v_star)", "eta = (P.Jc @ v)"),
+    "transposed_R": (ov, "make_problem", "data.append((sign * R[m]).ravel())",
+                     "data.append((sign * R[m].transpose(0, 2, 1)).ravel())"),
+    "d_contact_sign": (ov, "make_problem", "(-1.0, node_j, node_j >= 0)", "(1.0, node_j, node_j >= 0)"),
+    "gamma_transposed": (ov, "gamma_blocks", '"kab,kb,kcb->kac"', '"kba,kb,kbc->kac"'),
+    "w_no_square": (ov, "frobenius_w", "s = np.asarray(A.multiply(A).sum(axis=1)).ravel()",
+                    "s = np.asarray(abs(A).sum(axis=1)).ravel() ** 2"),
+    "w_untied": (ov, "frobenius_w", "w[dofs] = d[dofs].sum() / s[dofs].sum()", "pass"),
+    "friction_radius": (ov, "project_strict", "radius = mu * lam[:, 0]", "radius = mu * np.abs(lam_star[:, 0])"),
+    "slip_scale": (ov, "project_strict", "radius / np.where(inside, 1.0, rho)",
+                   "rho / np.where(inside, 1.0, radius + 1e-300)"),
+    "theta_no_sqrt": (ov, "sweep", "theta = math.sqrt(math.fsum(dv * dv))", "theta = math.fsum(dv * dv)"),
+    "prox_no_scale": (ov, "project_proximal", "/ (1.0 + mu[edge] ** 2)", "/ (1.0 + mu[edge])"),
+    "stop_off_by_one": (ov, "solve", "if r.theta < theta_th or l == l_max:",
+                        "if r.theta < theta_th or l == l_max + 1:"),
+    "adjoint_no_transpose": (oadj, "adjoint", "np.linalg.solve((np.eye(n) - D).T,",
+                             "np.linalg.solve((np.eye(n) - D),"),
+    "adjoint_mu_sign": (oadj, "strict_jacobian", "dmu[1:] = ln * t", "dmu[1:] = -ln * t"),
+}
+
+
+def _pin_suite():
+    """Run the pins; return True if all pass."""
+    rng = lambda: np.random.default_rng(1234)
+    calls = [
+        lambda: pins.test_strict_projection_is_disk_projection(rng()),
+        lambda: pins.test_strict_projection_tie_cases(),
+        lambda: pins.test_proximal_projection_is_euclidean_cone_projection(rng()),
+        lambda: pins.test_lemma2_slip_derivative_norm_is_mu(rng()),
+        lambda: pins.test_frobenius_w_is_the_tied_minimiser(rng()),
+        lambda: pins.test_prop3_surrogate_delassus_is_diagonal(rng()),
+        lambda: pins.test_single_point_mass_matches_textbook_coulomb(rng()),
+        lambda: pins.test_independent_point_masses_one_sweep(rng()),
+        lambda: pins.test_iterates_satisfy_surrogate_scc_exactly(rng()),
+        lambda: pins.test_theta_is_two_norm_of_the_update(rng()),
+        lambda: pins.test_two_point_masses_d_contact_match_textbook_impact(rng(), True),
+        lambda: pins.test_gamma_blocks_are_the_dense_product_for_any_diagonal_w(rng()),
+        lambda: pins.test_solve_counts_iterations_like_alg1(rng()),
+        lambda: pins.test_fixed_point_is_in_enumerated_scc_set(2, 17),
+        lambda: pins.test_fixed_point_is_in_enumerated_scc_set(3, 21),
+        lambda: pins.test_dense_adjoint_matches_central_differences(0),
+    ]
+    for call in calls:
+        try:
+            with np.errstate(all="ignore"):
+                call()
+        except (AssertionError, np.linalg.LinAlgError, ValueError, FloatingPointError,
+                ZeroDivisionError, IndexError):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, monkeypatch):
+    module, fname, old, new = MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(getattr(module, fname)))
+    assert src.count(old) == 1, f"mutant {name} no longer matches the oracle source"
+    ns = dict(vars(module))
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
+    monkeypatch.setattr(module, fname, ns[fname])
+    monkeypatch.setattr(pins, fname, ns[fname], raising=False)
+    if module is ov:
+        # functions imported by name elsewhere in the oracle follow the mutant
+        monkeypatch.setattr(oadj, fname, ns[fname], raising=False)
+        import oracle.delassus as odel
+        monkeypatch.setattr(odel, fname, ns[fname], raising=False)
+    assert not _pin_suite(), f"no pin caught the planted mistake {name!r}"
+
+
+def test_unmutated_oracle_passes_the_suite():
+    assert _pin_suite()
