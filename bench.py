@@ -1,0 +1,312 @@
+"""Benchmark of the V-FPI hot path on GB300.
+
+Workload: the 128x128x32 mass-spring lattice draped on a sinusoid+noise
+heightfield (1,572,864 DOF, 13,716,856 3x3 blocks, 16,384 contacts with
+mu ~ U[0.2, 0.8]), FP32 with FP64 residual reduction and position update.  One
+step = one time step of the solver: reset the warm start, run Alg. 1 to
+theta < theta_th or l = l_max (200) on the device, integrate x += h v_hat in
+FP64.  ``value`` is DOF x sweeps / device time (DOF-iterations per second).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(a bounded number of sweeps per step).  Under torchrun each rank runs an
+independent replica (a single scene does not shard without an exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import resource
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V-FPI DOF-iters/s & % HBM roofline; batched env-steps/s; adjoint/forward ratio"
+UNIT = "DOF-iter/s"
+WORKLOAD = "terrain_lattice_128x128x32"
+THETA_TH = 1e-6          # RMS residual threshold (m/s per DOF)
+L_MAX = 200
+FALLBACK_HBM_GBS = 6800.0
+
+# ncu DRAM traffic (read + write bytes per sweep) of the solve kernel, keyed by
+# the hash of the CUDA sources it was captured from; stale entries read as null.
+NCU_TRAFFIC = {}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2201_09212_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes_per_sweep(sc, esz=4) -> int:
+    """Bytes one sweep must move at minimum: every block and column index once,
+    the row pointers, v^l read, b read, v^{l+1} written, W read, the contact
+    records (R, mu, phi, node ids: 48 B) and lambda written (12 B)."""
+    N, n, nnzb, n_c = sc.n_nodes, sc.n, sc.nnzb, sc.n_c
+    return (nnzb * (9 * esz + 4) + 4 * (N + 1) + 3 * esz * n + esz * N + n_c * (48 + 12))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(sc, sweeps: int):
+    """Time the FP64 oracle's V-FPI sweeps on this host; returns
+    (DOF-iter/s, effective cores, seconds)."""
+    from oracle import vfpi as ov
+    P = ov.make_problem(sc.row_ptr, sc.col_idx, sc.vals, sc.b, sc.node_i, sc.node_j, sc.R,
+                        sc.mu, sc.phi)
+    w = ov.frobenius_w(P)
+    v = np.asarray(sc.v0, dtype=np.float64)
+    ov.sweep(P, w, v)  # warm
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        v = ov.sweep(P, w, v).v_next
+    dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return sc.n * sweeps / dt, max(1, round(cpu / dt)), dt
+
+
+def run_reference(args, sc):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    per_step = 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sc, 1)
+    t0 = time.perf_counter()
+    rates, cores = [], 1
+    for _ in range(args.steps):
+        r, cores, _ = cpu_oracle_rate(sc, per_step)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dof": sc.n, "blocks": sc.nnzb, "contacts": sc.n_c},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} FP64 oracle sweeps per step of the full workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dims", default="128,128,32")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    dims = tuple(int(x) for x in args.dims.split(","))
+
+    from paper_2201_09212_gb300 import scenes
+    sc = scenes.terrain_lattice(dims=dims)
+    if args.impl == "reference":
+        run_reference(args, sc)
+        return
+
+    import torch
+    ws, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the solver has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2201_09212_gb300 import vfpi
+    stream = torch.cuda.Stream()
+    s = vfpi.Solver.from_scene(sc, theta_th=THETA_TH, l_max=L_MAX, norm="rms", stream=stream)
+    dev = torch.device("cuda", local)
+    v0 = torch.from_numpy(sc.v0).to(dev)
+    x = torch.from_numpy(sc.x0).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        s.set_velocity(v0)
+        s.solve_async()
+        s.integrate(x)
+
+    for _ in range(args.warmup):
+        step()
+        s.status()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, kms = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            it, th, _ = s.status()
+            iters.append(int(it[0]))
+            kms.append(s.last_kernel_ms())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        dist.barrier()
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    units = sc.n * sum(iters) * ws
+    value = units / elapsed
+    launches_per_step = 3  # warm-start conversion, solve, integrate
+
+    # end to end through the public API with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    b_h, phi_h, v_h, x_h = pin(sc.b), pin(sc.phi), pin(sc.v0), pin(sc.x0)
+    lam_h = torch.empty(3 * sc.n_c, dtype=torch.float32).pin_memory()
+    v_out = torch.empty_like(v_h).pin_memory()
+    e2e_iters = []
+
+    def e2e_step():
+        s.set_rhs(b_h, phi_h)
+        v_out.copy_(v_h)
+        r = s.solve(v_out, out_v=v_out, out_lam=lam_h)
+        s.integrate(x_h)
+        return r
+
+    for _ in range(args.warmup):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_iters.append(e2e_step().iters)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = sc.n * sum(e2e_iters) * ws / e2e_t
+    h2d = 4 * (sc.n + sc.n_c + sc.n) + 8 * sc.n
+    d2h = 4 * (sc.n + 3 * sc.n_c) + 8 * sc.n
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    bps = algorithmic_bytes_per_sweep(sc)
+    k_avg = float(np.mean(kms)) / 1e3
+    it_avg = float(np.mean(iters))
+    achieved = bps * it_avg / k_avg / 1e9
+    peak, peak_kind = peaks()
+    tr = NCU_TRAFFIC.get(source_hash())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": (tr * it_avg if tr else None),
+                "algorithmic_bytes_per_sweep": bps, "kernel": "k_solve_grid<float,256>",
+                "kernel_ms_avg": 1e3 * k_avg}
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, cores, dt = cpu_oracle_rate(sc, args.cpu_sweeps)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sweeps} FP64 oracle V-FPI sweeps of the full workload ({dt:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dof": sc.n, "blocks": sc.nnzb, "contacts": sc.n_c,
+                   "theta_th": THETA_TH, "residual_norm": "rms", "l_max": L_MAX,
+                   "iters_per_step": it_avg, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (549 MB of blocks streamed per sweep)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

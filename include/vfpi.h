@@ -1,0 +1,186 @@
+/*
+ * vfpi.h -- C ABI of the GB300 (sm_103a) velocity fixed-point iteration (V-FPI)
+ * contact solver of Lee, Lee & Lee, "Large-Dimensional Multibody Dynamics
+ * Simulation Using Contact Nodalization and Diagonalization" (arXiv 2201.09212).
+ *
+ * Problem (eq. lindyn, eq. scc): find v in R^n, lambda in R^{3 n_c} with
+ *     A v = b + J_c^T lambda
+ * and, per contact m, the Signorini-Coulomb conditions on
+ *     u_m = J_{c,m} v + phi_m e_n,   lambda_m = [lambda_n; lambda_t1; lambda_t2].
+ * A is SPD, given as 3x3 block-sparse rows (one block row per node, n = 3N).
+ * Contacts are nodal (eq. jcnode): J_{c,m} = [.. R_m ..] for an S-contact on
+ * node i, [.. R_m .. -R_m ..] for a D-contact between nodes i and j, with the
+ * rows of R_m the contact normal and two tangents (global -> contact frame).
+ *
+ * Method (Alg. 1 with Alg. 2): with a diagonal step matrix W whose three
+ * entries are tied on every node in contact (Prop. 3),
+ *     v*      = v^l - W (A v^l - b)                         (eq. pgd1)
+ *     eta_m   = J_{c,m} v*,  gamma_m = w_i (+ w_j)          (eq. subp, eq. diagonal)
+ *     lambda* = -(eta_m + phi_m e_n) / gamma_m,  lambda_m = ProjectFC(lambda*)  (Alg. 2)
+ *     v^{l+1} = v* + W J_c^T lambda                         (eq. vup)
+ *     theta   = ||v^{l+1} - v^l||,  stop if theta < theta_th or l = l_max   (Alg. 1)
+ * ProjectFC is the strict operator (eq. operator): lambda_n = max(lambda*_n, 0),
+ * tangential part projected onto the disk of radius mu lambda_n.
+ *
+ * Conventions for every entry point
+ *  - Arrays are in the context's dtype (VFPI_F32 -> float, VFPI_F64 -> double)
+ *    unless stated; positions are always double.
+ *  - Every array pointer may be host memory (pageable or pinned) or device
+ *    memory; the library asks the CUDA runtime which.  Inputs are copied into
+ *    library-owned device memory (re-laid out); the caller keeps ownership of
+ *    everything it passes and may free it once the call returns.
+ *  - Work is enqueued on the stream given to vfpi_create (NULL = legacy default
+ *    stream).  Calls that return host scalars, or write to host arrays,
+ *    synchronise that stream; the others are asynchronous.
+ *  - Errors are reported by the return status and never abort the process;
+ *    vfpi_last_error() returns a message.  VFPI_NOT_CONVERGED is a soft status:
+ *    the last iterate is still returned.
+ *  - Node order is the caller's throughout; velocities are [3N] (x, y, z per
+ *    node), impulses [n_c * 3] in contact order (lambda_n, lambda_t1, lambda_t2).
+ */
+#ifndef VFPI_H
+#define VFPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vfpi_ctx* vfpi_t;
+
+typedef enum {
+  VFPI_OK = 0,
+  VFPI_NOT_CONVERGED = 1,        /* l_max reached with theta >= theta_th       */
+  VFPI_ERR_INVALID_ARG = -1,     /* bad sizes, indices, pattern or options      */
+  VFPI_ERR_NONFINITE = -2,       /* NaN/Inf in the data or in an iterate        */
+  VFPI_ERR_CUDA = -3,            /* a CUDA runtime call failed                  */
+  VFPI_ERR_OOM = -4,             /* device allocation failed                    */
+  VFPI_ERR_TIMEOUT = -5,         /* a bounded device-side wait ran out          */
+  VFPI_ERR_CONTACT_OVERLAP = -6, /* a node appears in more than one contact     */
+  VFPI_ERR_UNSUPPORTED = -7      /* option not available in this build          */
+} vfpi_status;
+
+enum { VFPI_F32 = 0, VFPI_F64 = 1 };
+/* Choice of W (Sec. IV.C): Frobenius-norm minimiser, alpha * I, or caller's. */
+enum { VFPI_W_FROBENIUS = 0, VFPI_W_SCALAR = 1, VFPI_W_USER = 2 };
+/* ProjectFC (eq. operator).  Only the strict operator is built. */
+enum { VFPI_OP_STRICT = 0, VFPI_OP_PROXIMAL = 1 };
+/* Residual of Alg. 1: ||dv||_2 (paper) or ||dv||_2 / sqrt(n). */
+enum { VFPI_NORM_ABS = 0, VFPI_NORM_RMS = 1 };
+
+/* A in 3x3 block-sparse-row form (Sec. V.A stores A sparse; blocks here).
+ * row_ptr [n_nodes+1], col_idx [nnzb] strictly increasing per row with the
+ * diagonal block present, vals [nnzb * 9] row-major blocks.  The full
+ * (symmetric) pattern is given; no symmetry is assumed by the solver. */
+typedef struct {
+  int32_t n_nodes;
+  int32_t nnzb;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* vals;
+} vfpi_bsr;
+
+/* Nodal contacts (eq. jcnode).  node_j[m] = -1 marks an S-contact; node_j may
+ * be NULL when every contact is an S-contact.  R [n_c * 9] row-major with rows
+ * n, t1, t2 (orthonormal, det +1, checked to 1e-4); mu [n_c] >= 0; phi [n_c]
+ * the normal offset of eq. (scc).  Every node may appear in at most one
+ * contact (Prop. 3 needs it; else VFPI_ERR_CONTACT_OVERLAP). */
+typedef struct {
+  int32_t n_c;
+  const int32_t* node_i;
+  const int32_t* node_j;
+  const void* R;
+  const void* mu;
+  const void* phi;
+} vfpi_contacts;
+
+typedef struct {
+  int32_t dtype;           /* VFPI_F32 | VFPI_F64                                  */
+  int32_t w_mode;          /* VFPI_W_*                                             */
+  double alpha;            /* VFPI_W_SCALAR: W = alpha I                            */
+  const void* w_user;      /* VFPI_W_USER: [3N], tied on contact nodes              */
+  double theta_th;         /* Alg. 1 threshold                                     */
+  int32_t l_max;           /* Alg. 1 iteration cap (>= 1)                          */
+  int32_t operator_;       /* VFPI_OP_*                                            */
+  int32_t residual_norm;   /* VFPI_NORM_*                                          */
+  int32_t n_scenes;        /* 0 or 1: one problem; > 1: independent scenes          */
+  const int32_t* scene_ptr;/* [n_scenes+1] node offsets of the scenes (batched)     */
+  int32_t block_threads;   /* 0 = default; threads per CTA of the solve kernel       */
+  int32_t force_path;      /* 0 = auto, 1 = grid-wide kernel, 2 = CTA-per-scene      */
+  int32_t reserved[6];
+} vfpi_opts;
+
+/* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,
+ * strict operator, absolute norm, one scene. */
+void vfpi_default_opts(vfpi_opts* o);
+
+/* Build a solver for A, b, J_c (eq. lindyn, eq. jcnode).  Validates A's pattern
+ * (sorted columns, diagonal present, no block between two scenes), finiteness,
+ * and the contacts; lays A out for the device; chooses W (Sec. IV.C, once per
+ * A, "recycled" as the paper does); sets the warm start to zero.  h is the
+ * time step used by vfpi_integrate.  On success *out owns device memory until
+ * vfpi_destroy. */
+vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* Jc,
+                        double h, const vfpi_opts* o, void* cuda_stream, vfpi_t* out);
+
+/* Replace the values of A (same pattern; W is recomputed), b and/or the
+ * contact set (re-validated; W re-tied).  NULL leaves that part unchanged. */
+vfpi_status vfpi_update(vfpi_t ctx, const void* A_vals, const void* b, const vfpi_contacts* Jc);
+
+/* Per-time-step inputs without re-validation: b [3N] and/or phi [n_c] (NULL
+ * keeps the old value).  Asynchronous for device pointers. */
+vfpi_status vfpi_set_rhs(vfpi_t ctx, const void* b, const void* phi);
+
+/* Warm start v^1 [3N] (Sec. V.A, "warm start"); asynchronous for device input. */
+vfpi_status vfpi_set_velocity(vfpi_t ctx, const void* v);
+/* Current iterate [3N] and the impulses of the last sweep [n_c * 3]. */
+vfpi_status vfpi_get_velocity(vfpi_t ctx, void* v);
+vfpi_status vfpi_get_lambda(vfpi_t ctx, void* lambda);
+/* The diagonal of W [3N] (Sec. IV.C). */
+vfpi_status vfpi_get_w(vfpi_t ctx, void* w);
+
+/* Exactly one V-FPI sweep (eq. pgd1, subp, Alg. 2, eq. vup) from the current
+ * iterate; *theta_out (nullable, synchronises) gets ||v^{l+1} - v^l||. */
+vfpi_status vfpi_step(vfpi_t ctx, double* theta_out);
+
+/* Alg. 1 inner loop to theta < theta_th or l = l_max, entirely on the device
+ * (no per-iteration host round trip).  v_inout (nullable): warm start in, v_hat
+ * out; lambda_out (nullable); iters_out/theta_out (nullable) for one scene,
+ * or arrays of n_scenes entries in batched mode.  Returns VFPI_NOT_CONVERGED
+ * if some scene hit l_max. */
+vfpi_status vfpi_solve(vfpi_t ctx, void* v_inout, void* lambda_out, int32_t* iters_out,
+                       double* theta_out);
+
+/* Enqueue the solve from the current iterate without synchronising (CUDA-graph
+ * capturable); read the outcome later with vfpi_get_status. */
+vfpi_status vfpi_solve_async(vfpi_t ctx);
+/* Synchronise and read the last solve's iteration counts and residuals
+ * (arrays of n_scenes entries in batched mode; nullable). */
+vfpi_status vfpi_get_status(vfpi_t ctx, int32_t* iters_out, double* theta_out);
+
+/* State update x_{k+1} = x_k + h v_hat (eq. disc_dyn) in FP64 on the device;
+ * x_inout [3N] double. */
+vfpi_status vfpi_integrate(vfpi_t ctx, double* x_inout);
+
+/* y = A x with the context's A (x, y [3N]); the only super-linear product of
+ * the method (Sec. III.F), exposed for residual checks and dynamics harnesses. */
+vfpi_status vfpi_matvec(vfpi_t ctx, const void* x, void* y);
+
+/* Device time in milliseconds of the most recent solve kernel, measured with
+ * CUDA events recorded on the context's stream around that launch. */
+vfpi_status vfpi_last_kernel_ms(vfpi_t ctx, float* ms);
+
+/* Sizes of the device layout: [0] padded nodes, [1] slices of 32 rows,
+ * [2] stored block slots (incl. padding), [3] kernel path (1 grid, 2 CTA per
+ * scene), [4] CTAs of the solve launch, [5] threads per CTA. */
+vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info6);
+
+const char* vfpi_last_error(vfpi_t ctx);
+const char* vfpi_status_string(vfpi_status s);
+void vfpi_destroy(vfpi_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VFPI_H */

@@ -1,0 +1,806 @@
+// C ABI of libvfpi (declared in include/vfpi.h): argument checking, input
+// staging, layout set-up, contact bookkeeping and dispatch to the per-dtype
+// launchers.  Host code only; every step of the solve runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "vfpi_internal.h"
+
+using vfpi::Launch;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+#define VFPI_TRY_CUDA(expr)                                                   \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr);                    \
+  } while (0)
+
+vfpi_status cuda_fail(vfpi_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "CUDA error %s (%s) in %s", cudaGetErrorName(e),
+                cudaGetErrorString(e), what);
+  if (c) c->err = buf; else g_create_error = buf;
+  return e == cudaErrorMemoryAllocation ? VFPI_ERR_OOM : VFPI_ERR_CUDA;
+}
+
+vfpi_status arg_fail(vfpi_ctx* c, vfpi_status st, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return st;
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+// Copy n bytes from caller memory (host or device) into host vector storage.
+cudaError_t to_host(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if (!on_device(src)) {
+    std::memcpy(dst, src, bytes);
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+// Make the staging buffer at least `bytes` long (waits for earlier users).
+cudaError_t ensure_stage(vfpi_ctx* c, size_t bytes) {
+  if (bytes <= c->stage_bytes) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  if (c->d_stage) cudaFree(c->d_stage);
+  c->d_stage = nullptr;
+  c->stage_bytes = 0;
+  const size_t want = std::max<size_t>(bytes, 1 << 20);
+  if ((e = cudaMalloc(&c->d_stage, want)) != cudaSuccess) return e;
+  c->stage_bytes = want;
+  return cudaSuccess;
+}
+
+// Device view of caller memory: the pointer itself if it is device memory,
+// else a copy at byte offset `slot` of the staging buffer (grown if needed;
+// growing invalidates earlier views, so multi-view callers size it first).
+cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot, const void** out) {
+  if (on_device(src)) {
+    *out = src;
+    return cudaSuccess;
+  }
+  cudaError_t e = ensure_stage(c, slot + bytes);
+  if (e != cudaSuccess) return e;
+  char* dst = static_cast<char*>(c->d_stage) + slot;
+  *out = dst;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+}
+
+// Write `bytes` of device data to caller memory (host or device).
+cudaError_t to_caller(vfpi_ctx* c, void* dst, const void* dev_src, size_t bytes) {
+  if (bytes == 0) return cudaSuccess;
+  if (on_device(dst)) return cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+// Where a kernel should write an output bound for caller memory: the caller's
+// pointer if it is device memory, else the staging buffer at `slot`.
+cudaError_t out_view(vfpi_ctx* c, void* dst, size_t bytes, size_t slot, void** out) {
+  if (on_device(dst)) {
+    *out = dst;
+    return cudaSuccess;
+  }
+  cudaError_t e = ensure_stage(c, slot + bytes);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<char*>(c->d_stage) + slot;
+  return cudaSuccess;
+}
+
+void free_all(vfpi_ctx* c) {
+  void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_vals, c->d_cols, c->d_b, c->d_w,
+                  c->d_v0, c->d_v1, c->d_t0, c->d_t1, c->d_cslot, c->d_node_map, c->d_row_ptr, c->d_ds,
+                  c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi,
+                  c->d_lam, c->d_lam_star, c->d_scene_slice, c->d_scene_d, c->d_order,
+                  c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
+                  c->d_status, c->d_theta, c->d_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// dispatch helpers on dtype
+// ---------------------------------------------------------------------------
+
+#define DISPATCH(c, call) ((c)->dtype == VFPI_F64 ? Launch<double>::call : Launch<float>::call)
+
+// ---------------------------------------------------------------------------
+// contacts
+// ---------------------------------------------------------------------------
+
+vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
+  const int n_c = J ? J->n_c : 0;
+  if (n_c < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "n_c < 0");
+  if (n_c > 0 && (!J->node_i || !J->R || !J->mu || !J->phi))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "contacts: node_i, R, mu and phi are required");
+  std::vector<int32_t> ni(n_c), nj(n_c, -1);
+  std::vector<double> R(9 * (size_t)n_c), mu(n_c), phi(n_c);
+  cudaStream_t s = c->stream;
+  VFPI_TRY_CUDA(to_host(ni.data(), J ? J->node_i : nullptr, 4 * (size_t)n_c, s));
+  if (J && J->node_j) VFPI_TRY_CUDA(to_host(nj.data(), J->node_j, 4 * (size_t)n_c, s));
+  {
+    std::vector<unsigned char> raw(c->esz * 11 * (size_t)n_c);
+    if (n_c > 0) {
+      VFPI_TRY_CUDA(to_host(raw.data(), J->R, c->esz * 9 * (size_t)n_c, s));
+      VFPI_TRY_CUDA(to_host(raw.data() + c->esz * 9 * (size_t)n_c, J->mu, c->esz * (size_t)n_c, s));
+      VFPI_TRY_CUDA(to_host(raw.data() + c->esz * 10 * (size_t)n_c, J->phi, c->esz * (size_t)n_c, s));
+    }
+    for (size_t k = 0; k < 11 * (size_t)n_c; ++k) {
+      const double v = c->dtype == VFPI_F64 ? reinterpret_cast<const double*>(raw.data())[k]
+                                            : (double)reinterpret_cast<const float*>(raw.data())[k];
+      if (k < 9 * (size_t)n_c) R[k] = v;
+      else if (k < 10 * (size_t)n_c) mu[k - 9 * (size_t)n_c] = v;
+      else phi[k - 10 * (size_t)n_c] = v;
+    }
+  }
+  // validation
+  std::vector<int32_t> owner(c->N, -1);
+  for (int m = 0; m < n_c; ++m) {
+    const int i = ni[m], j = nj[m];
+    if (i < 0 || i >= c->N || j < -1 || j >= c->N || i == j)
+      return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": node index out of range");
+    if (j >= 0 && c->h_node_scene[i] != c->h_node_scene[j])
+      return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": D-contact across scenes");
+    for (int q : {i, j}) {
+      if (q < 0) continue;
+      if (owner[q] >= 0)
+        return arg_fail(c, VFPI_ERR_CONTACT_OVERLAP,
+                        "node " + std::to_string(q) + " is in contacts " + std::to_string(owner[q]) +
+                            " and " + std::to_string(m));
+      owner[q] = m;
+    }
+    const double* r = &R[9 * (size_t)m];
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(r[k])) return arg_fail(c, VFPI_ERR_NONFINITE, "contact frame not finite");
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double d = r[3 * a] * r[3 * b] + r[3 * a + 1] * r[3 * b + 1] + r[3 * a + 2] * r[3 * b + 2];
+        if (std::fabs(d - (a == b ? 1.0 : 0.0)) > 1e-4)
+          return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": R is not orthonormal");
+      }
+    const double det = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
+                       r[2] * (r[3] * r[7] - r[4] * r[6]);
+    if (det < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": det R < 0");
+    if (!std::isfinite(mu[m]) || !std::isfinite(phi[m]))
+      return arg_fail(c, VFPI_ERR_NONFINITE, "contact mu/phi not finite");
+    if (mu[m] < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": mu < 0");
+  }
+  // internal order: by internal node i (groups contacts by scene, consecutive
+  // rows read consecutive records)
+  std::vector<int32_t> perm(n_c);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) {
+    return c->h_node_map[ni[a]] < c->h_node_map[ni[b]];
+  });
+  c->h_cperm = perm;
+  c->h_ci.assign(n_c, -1);
+  c->h_cj.assign(n_c, -1);
+  std::vector<int32_t> cslot(c->n_pad, -1), dlist;
+  std::vector<int32_t> scene_d(c->n_scenes + 1, 0);
+  std::vector<unsigned char> Rint(c->esz * 9 * (size_t)n_c), muint(c->esz * (size_t)n_c),
+      phint(c->esz * (size_t)n_c);
+  auto put = [&](std::vector<unsigned char>& buf, size_t k, double v) {
+    if (c->dtype == VFPI_F64) reinterpret_cast<double*>(buf.data())[k] = v;
+    else reinterpret_cast<float*>(buf.data())[k] = (float)v;
+  };
+  for (int m = 0; m < n_c; ++m) {
+    const int e = perm[m];
+    const int pi = c->h_node_map[ni[e]];
+    const int pj = nj[e] >= 0 ? c->h_node_map[nj[e]] : -1;
+    c->h_ci[m] = pi;
+    c->h_cj[m] = pj;
+    cslot[pi] = m;
+    if (pj >= 0) {
+      cslot[pj] = m;
+      dlist.push_back(m);
+      scene_d[c->h_node_scene[ni[e]] + 1]++;
+    }
+    for (int q = 0; q < 9; ++q) put(Rint, (size_t)q * n_c + m, R[9 * (size_t)e + q]);
+    put(muint, m, mu[e]);
+    put(phint, m, phi[e]);
+  }
+  for (int q = 0; q < c->n_scenes; ++q) scene_d[q + 1] += scene_d[q];
+  // (re)allocate contact arrays once earlier work on the stream has finished
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  c->n_c = n_c;
+  c->n_d = (int)dlist.size();
+  int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist};
+  for (auto p : ip) if (p) cudaFree(p);
+  void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_lam, c->d_lam_star};
+  for (auto p : vp) if (p) cudaFree(p);
+  VFPI_TRY_CUDA(dalloc(&c->d_ci, 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_cj, 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_cperm, 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_dlist, 4 * dlist.size()));
+  VFPI_TRY_CUDA(dalloc(&c->d_cR, c->esz * 9 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_cmu, c->esz * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_cphi, c->esz * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_lam, c->esz * 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_lam_star, c->esz * 4 * (size_t)n_c));
+  cudaStream_t st = c->stream;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_ci, c->h_ci.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cj, c->h_cj.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cperm, perm.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_dlist, dlist.data(), 4 * dlist.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cR, Rint.data(), Rint.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cphi, phint.data(), phint.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_lam, 0, c->esz * 4 * (size_t)n_c, st));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_lam_star, 0, c->esz * 4 * (size_t)n_c, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cslot, cslot.data(), 4 * (size_t)c->n_pad, cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_scene_d, scene_d.data(), 4 * scene_d.size(), cudaMemcpyHostToDevice, st));
+  // host vectors must outlive the async copies
+  VFPI_TRY_CUDA(cudaStreamSynchronize(st));
+  return VFPI_OK;
+}
+
+vfpi_status set_w(vfpi_ctx* c) {
+  if (c->opts.w_mode == VFPI_W_USER) {
+    if (!c->opts.w_user) return arg_fail(c, VFPI_ERR_INVALID_ARG, "w_mode USER needs w_user");
+    const size_t bytes = c->esz * 3 * (size_t)c->N;
+    std::vector<unsigned char> raw(bytes);
+    VFPI_TRY_CUDA(to_host(raw.data(), c->opts.w_user, bytes, c->stream));
+    auto wv = [&](size_t k) {
+      return c->dtype == VFPI_F64 ? reinterpret_cast<const double*>(raw.data())[k]
+                                  : (double)reinterpret_cast<const float*>(raw.data())[k];
+    };
+    // Prop. 3: the three entries of a contact node (six of a D-contact) are tied
+    std::vector<int32_t> inv(c->n_pad, -1);
+    for (int i = 0; i < c->N; ++i) inv[c->h_node_map[i]] = i;
+    for (int m = 0; m < c->n_c; ++m) {
+      const int i = inv[c->h_ci[m]];
+      const double w0 = wv(3 * (size_t)i);
+      for (int node : {c->h_ci[m], c->h_cj[m]}) {
+        if (node < 0) continue;
+        const int e = inv[node];
+        for (int a = 0; a < 3; ++a)
+          if (wv(3 * (size_t)e + a) != w0)
+            return arg_fail(c, VFPI_ERR_INVALID_ARG, "user W is not tied on contact nodes (Prop. 3)");
+      }
+    }
+    for (size_t k = 0; k < 3 * (size_t)c->N; ++k)
+      if (!std::isfinite(wv(k)) || wv(k) <= 0)
+        return arg_fail(c, VFPI_ERR_INVALID_ARG, "user W must be positive and finite");
+    const void* dv;
+    VFPI_TRY_CUDA(device_view(c, c->opts.w_user, bytes, 0, &dv));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_w, 0, c->esz * 4 * (size_t)c->n_pad, c->stream));
+    VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dv, c->d_w)));
+    return VFPI_OK;
+  }
+  if (c->opts.w_mode == VFPI_W_SCALAR && !(c->opts.alpha > 0 && std::isfinite(c->opts.alpha)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "w_mode SCALAR needs alpha > 0");
+  VFPI_TRY_CUDA(DISPATCH(c, make_w(c)));
+  return VFPI_OK;
+}
+
+vfpi_status read_err(vfpi_ctx* c, int* flags) {
+  VFPI_TRY_CUDA(cudaMemcpyAsync(flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return VFPI_OK;
+}
+
+// A's values: checked finite, then scattered into the sliced-ELL layout.  With
+// store_cols the pattern (drow, dcol: device copies) is laid out too; without
+// it only the values are replaced and the stored pattern is reused.
+vfpi_status set_values(vfpi_ctx* c, const int32_t* drow, const int32_t* dcol, const void* vals,
+                       bool store_cols, size_t slot) {
+  const size_t vbytes = c->esz * 9 * (size_t)c->nnzb;
+  const void* dv;
+  VFPI_TRY_CUDA(device_view(c, vals, vbytes, slot, &dv));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  VFPI_TRY_CUDA(DISPATCH(c, check_finite(dv, 9 * (int64_t)c->nnzb, c->d_err, c->stream)));
+  int flags = 0;
+  vfpi_status st = read_err(c, &flags);
+  if (st != VFPI_OK) return st;
+  if (flags) return arg_fail(c, VFPI_ERR_NONFINITE, "A has non-finite values");
+  VFPI_TRY_CUDA(DISPATCH(c, build_layout(c, drow, dcol, dv, store_cols)));
+  return VFPI_OK;
+}
+
+vfpi_status set_b(vfpi_ctx* c, const void* b) {
+  const size_t bytes = c->esz * 3 * (size_t)c->N;
+  const void* db;
+  VFPI_TRY_CUDA(device_view(c, b, bytes, 0, &db));
+  VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, db, c->d_b)));
+  return VFPI_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void vfpi_default_opts(vfpi_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->dtype = VFPI_F32;
+  o->w_mode = VFPI_W_FROBENIUS;
+  o->alpha = 0.0;
+  o->theta_th = 1e-5;
+  o->l_max = 200;
+  o->operator_ = VFPI_OP_STRICT;
+  o->residual_norm = VFPI_NORM_ABS;
+  o->n_scenes = 1;
+}
+
+const char* vfpi_status_string(vfpi_status s) {
+  switch (s) {
+    case VFPI_OK: return "VFPI_OK";
+    case VFPI_NOT_CONVERGED: return "VFPI_NOT_CONVERGED";
+    case VFPI_ERR_INVALID_ARG: return "VFPI_ERR_INVALID_ARG";
+    case VFPI_ERR_NONFINITE: return "VFPI_ERR_NONFINITE";
+    case VFPI_ERR_CUDA: return "VFPI_ERR_CUDA";
+    case VFPI_ERR_OOM: return "VFPI_ERR_OOM";
+    case VFPI_ERR_TIMEOUT: return "VFPI_ERR_TIMEOUT";
+    case VFPI_ERR_CONTACT_OVERLAP: return "VFPI_ERR_CONTACT_OVERLAP";
+    case VFPI_ERR_UNSUPPORTED: return "VFPI_ERR_UNSUPPORTED";
+  }
+  return "unknown status";
+}
+
+const char* vfpi_last_error(vfpi_t c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void vfpi_destroy(vfpi_t c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* Jc, double h,
+                        const vfpi_opts* o, void* cuda_stream, vfpi_t* out) {
+  g_create_error.clear();
+  if (!out) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A || !b || !o) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "A, b and opts are required");
+  if (o->dtype != VFPI_F32 && o->dtype != VFPI_F64)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "dtype must be VFPI_F32 or VFPI_F64");
+  if (o->operator_ != VFPI_OP_STRICT)
+    return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "only the strict operator is built");
+  if (o->l_max < 1) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "l_max must be >= 1");
+  if (o->w_mode < VFPI_W_FROBENIUS || o->w_mode > VFPI_W_USER)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "unknown w_mode");
+  if (o->residual_norm != VFPI_NORM_ABS && o->residual_norm != VFPI_NORM_RMS)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "unknown residual_norm");
+  if (A->n_nodes < 1 || A->nnzb < A->n_nodes || !A->row_ptr || !A->col_idx || !A->vals)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "A: need n_nodes >= 1, nnzb >= n_nodes and all arrays");
+  if ((int64_t)A->n_nodes * 32 > INT32_MAX)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "A: too many nodes");
+  if (!(std::isfinite(h))) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "h must be finite");
+  if (o->block_threads && o->block_threads != 64 && o->block_threads != 128 &&
+      o->block_threads != 256 && o->block_threads != 512)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
+
+  vfpi_ctx* c = new (std::nothrow) vfpi_ctx;
+  if (!c) return arg_fail(nullptr, VFPI_ERR_OOM, "host allocation failed");
+  c->dtype = o->dtype;
+  c->esz = o->dtype == VFPI_F64 ? 8 : 4;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->opts = *o;
+  c->h = h;
+  c->N = A->n_nodes;
+  c->nnzb = A->nnzb;
+  c->n_scenes = o->n_scenes > 1 ? o->n_scenes : 1;
+
+  auto fail = [&](vfpi_status st) {
+    g_create_error = c->err;
+    free_all(c);
+    delete c;
+    return st;
+  };
+  auto cuda_err = [&](cudaError_t e, const char* what) { return fail(cuda_fail(c, e, what)); };
+#define CREATE_CUDA(expr)                      \
+  do {                                         \
+    cudaError_t e__ = (expr);                  \
+    if (e__ != cudaSuccess) return cuda_err(e__, #expr); \
+  } while (0)
+#define CREATE_ST(expr)                        \
+  do {                                         \
+    vfpi_status s__ = (expr);                  \
+    if (s__ != VFPI_OK) return fail(s__);      \
+  } while (0)
+
+  // scenes
+  const int N = c->N;
+  c->h_scene_ptr.assign(c->n_scenes + 1, 0);
+  if (c->n_scenes > 1) {
+    if (!o->scene_ptr) { c->err = "n_scenes > 1 needs scene_ptr"; return fail(VFPI_ERR_INVALID_ARG); }
+    CREATE_CUDA(to_host(c->h_scene_ptr.data(), o->scene_ptr, 4 * ((size_t)c->n_scenes + 1), c->stream));
+    if (c->h_scene_ptr[0] != 0 || c->h_scene_ptr[c->n_scenes] != N) {
+      c->err = "scene_ptr must start at 0 and end at n_nodes";
+      return fail(VFPI_ERR_INVALID_ARG);
+    }
+    for (int q = 0; q < c->n_scenes; ++q)
+      if (c->h_scene_ptr[q + 1] <= c->h_scene_ptr[q]) {
+        c->err = "scene_ptr must be strictly increasing";
+        return fail(VFPI_ERR_INVALID_ARG);
+      }
+  } else {
+    c->h_scene_ptr[1] = N;
+  }
+  // internal numbering: every scene padded to a multiple of 32 rows
+  c->h_node_map.resize(N);
+  c->h_node_scene.resize(N);
+  c->h_scene_slice.assign(c->n_scenes + 1, 0);
+  int64_t base = 0;
+  for (int q = 0; q < c->n_scenes; ++q) {
+    c->h_scene_slice[q] = (int32_t)(base / 32);
+    for (int i = c->h_scene_ptr[q]; i < c->h_scene_ptr[q + 1]; ++i) {
+      c->h_node_map[i] = (int32_t)(base + (i - c->h_scene_ptr[q]));
+      c->h_node_scene[i] = q;
+    }
+    base += (int64_t)round_up(c->h_scene_ptr[q + 1] - c->h_scene_ptr[q], 32);
+  }
+  if (base > INT32_MAX) { c->err = "too many padded rows"; return fail(VFPI_ERR_INVALID_ARG); }
+  c->n_pad = (int)base;
+  c->n_slices = c->n_pad / 32;
+  c->h_scene_slice[c->n_scenes] = c->n_slices;
+
+  // row pointers on the host: check and derive the slice lengths
+  std::vector<int32_t> row_ptr(N + 1);
+  CREATE_CUDA(to_host(row_ptr.data(), A->row_ptr, 4 * ((size_t)N + 1), c->stream));
+  if (row_ptr[0] != 0 || row_ptr[N] != A->nnzb) {
+    c->err = "row_ptr must start at 0 and end at nnzb";
+    return fail(VFPI_ERR_INVALID_ARG);
+  }
+  c->h_slice_len.assign(c->n_slices, 0);
+  for (int i = 0; i < N; ++i) {
+    const int len = row_ptr[i + 1] - row_ptr[i];
+    if (len < 1 || len > N) { c->err = "row_ptr: every row needs 1..n_nodes blocks"; return fail(VFPI_ERR_INVALID_ARG); }
+    int32_t& sl = c->h_slice_len[c->h_node_map[i] / 32];
+    sl = std::max(sl, len);
+  }
+  c->h_slice_off.assign(c->n_slices, 0);
+  int64_t ent = 0;
+  for (int s = 0; s < c->n_slices; ++s) {
+    c->h_slice_off[s] = ent;
+    ent += c->h_slice_len[s];
+  }
+  c->n_entries = ent;
+
+  // device allocations
+  const size_t vec = c->esz * 4 * (size_t)c->n_pad;
+  CREATE_CUDA(dalloc(&c->d_slice_len, 4 * (size_t)c->n_slices));
+  CREATE_CUDA(dalloc(&c->d_slice_off, 8 * (size_t)c->n_slices));
+  CREATE_CUDA(dalloc(&c->d_vals, c->esz * 288 * (size_t)c->n_entries));
+  CREATE_CUDA(dalloc(&c->d_cols, 4 * 32 * (size_t)c->n_entries));
+  CREATE_CUDA(dalloc(&c->d_b, vec));
+  CREATE_CUDA(dalloc(&c->d_w, vec));
+  CREATE_CUDA(dalloc(&c->d_v0, vec));
+  CREATE_CUDA(dalloc(&c->d_v1, vec));
+  CREATE_CUDA(dalloc(&c->d_t0, vec));
+  CREATE_CUDA(dalloc(&c->d_t1, vec));
+  CREATE_CUDA(dalloc(&c->d_cslot, 4 * (size_t)c->n_pad));
+  CREATE_CUDA(dalloc(&c->d_node_map, 4 * (size_t)N));
+  CREATE_CUDA(dalloc(&c->d_row_ptr, 4 * ((size_t)N + 1)));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_row_ptr, row_ptr.data(), 4 * ((size_t)N + 1), cudaMemcpyHostToDevice, c->stream));
+  CREATE_CUDA(dalloc(&c->d_ds, 8 * 6 * (size_t)c->n_pad));
+  CREATE_CUDA(dalloc(&c->d_scene_slice, 4 * ((size_t)c->n_scenes + 1)));
+  CREATE_CUDA(dalloc(&c->d_scene_d, 4 * ((size_t)c->n_scenes + 1)));
+  CREATE_CUDA(dalloc(&c->d_order, 4 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_queue, 16));
+  CREATE_CUDA(dalloc(&c->d_norm_scale, 8 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_bar, 16));
+  CREATE_CUDA(dalloc(&c->d_err, 16));
+  CREATE_CUDA(dalloc(&c->d_iters, 4 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_status, 4 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_theta, 8 * (size_t)c->n_scenes));
+  CREATE_CUDA(cudaEventCreate(&c->ev0));
+  CREATE_CUDA(cudaEventCreate(&c->ev1));
+  cudaStream_t st = c->stream;
+  CREATE_CUDA(cudaMemcpyAsync(c->d_slice_len, c->h_slice_len.data(), 4 * (size_t)c->n_slices, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_slice_off, c->h_slice_off.data(), 8 * (size_t)c->n_slices, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_node_map, c->h_node_map.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_scene_slice, c->h_scene_slice.data(), 4 * ((size_t)c->n_scenes + 1), cudaMemcpyHostToDevice, st));
+  // largest scene first; per-scene norm scale
+  std::vector<int32_t> order(c->n_scenes);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return c->h_scene_ptr[a + 1] - c->h_scene_ptr[a] > c->h_scene_ptr[b + 1] - c->h_scene_ptr[b];
+  });
+  std::vector<double> nscale(c->n_scenes, 1.0);
+  if (o->residual_norm == VFPI_NORM_RMS)
+    for (int q = 0; q < c->n_scenes; ++q)
+      nscale[q] = 1.0 / std::sqrt(3.0 * (c->h_scene_ptr[q + 1] - c->h_scene_ptr[q]));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_order, order.data(), 4 * (size_t)c->n_scenes, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_norm_scale, nscale.data(), 8 * (size_t)c->n_scenes, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_v0, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_v1, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_b, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_w, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_t0, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_t1, 0, vec, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_cslot, 0xff, 4 * (size_t)c->n_pad, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_iters, 0, 4 * (size_t)c->n_scenes, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_status, 0, 4 * (size_t)c->n_scenes, st));
+  CREATE_CUDA(cudaMemsetAsync(c->d_theta, 0, 8 * (size_t)c->n_scenes, st));
+
+  // stage the pattern (front of the staging buffer), then validate it
+  const size_t off_col = 4 * ((size_t)N + 1);
+  const size_t off_scene = off_col + 4 * (size_t)c->nnzb;
+  const size_t off_vals = round_up(off_scene + 4 * (size_t)N, 256);
+  {
+    size_t need = off_vals;
+    if (!on_device(A->vals)) need += c->esz * 9 * (size_t)c->nnzb;
+    CREATE_CUDA(ensure_stage(c, need));
+  }
+  const int32_t *drow, *dcol, *dscene;
+  CREATE_CUDA(device_view(c, A->row_ptr, 4 * ((size_t)N + 1), 0, reinterpret_cast<const void**>(&drow)));
+  CREATE_CUDA(device_view(c, A->col_idx, 4 * (size_t)c->nnzb, off_col, reinterpret_cast<const void**>(&dcol)));
+  CREATE_CUDA(device_view(c, c->h_node_scene.data(), 4 * (size_t)N, off_scene,
+                          reinterpret_cast<const void**>(&dscene)));
+  CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  CREATE_CUDA(DISPATCH(c, validate_pattern(N, drow, dcol, dscene, c->d_err, st)));
+  {
+    int flags = 0;
+    CREATE_ST(read_err(c, &flags));
+    if (flags) {
+      c->err = std::string("A: invalid block pattern (") + ((flags & 1) ? "column out of range " : "") +
+               ((flags & 2) ? "columns not strictly increasing " : "") +
+               ((flags & 4) ? "block couples two scenes " : "") + ((flags & 16) ? "missing diagonal block" : "") + ")";
+      return fail(VFPI_ERR_INVALID_ARG);
+    }
+  }
+  CREATE_ST(set_values(c, drow, dcol, A->vals, true, off_vals));
+  // contacts, b, W
+  CREATE_ST(set_contacts(c, Jc));
+  {
+    const size_t bytes = c->esz * 3 * (size_t)N;
+    const void* db;
+    CREATE_CUDA(device_view(c, b, bytes, 0, &db));
+    CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    CREATE_CUDA(DISPATCH(c, check_finite(db, 3 * (int64_t)N, c->d_err, st)));
+    int flags = 0;
+    CREATE_ST(read_err(c, &flags));
+    if (flags) { c->err = "b has non-finite values"; return fail(VFPI_ERR_NONFINITE); }
+    CREATE_ST(set_b(c, b));
+  }
+  CREATE_ST(set_w(c));
+
+  // kernel path and launch shape
+  c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
+  if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
+  if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
+  c->nt = o->block_threads ? o->block_threads : (c->path == 1 ? 256 : 128);
+  CREATE_CUDA(DISPATCH(c, configure(c)));
+  CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
+  CREATE_CUDA(cudaStreamSynchronize(st));
+  if (c->stage_bytes > (64u << 20)) {  // the copy of a host-side A is no longer needed
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_bytes = 0;
+  }
+  *out = c;
+  return VFPI_OK;
+#undef CREATE_CUDA
+#undef CREATE_ST
+}
+
+#define CTX_CHECK(c)                                                            \
+  do {                                                                          \
+    if (!(c)) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "context is NULL"); \
+  } while (0)
+
+vfpi_status vfpi_update(vfpi_t c, const void* A_vals, const void* b, const vfpi_contacts* Jc) {
+  CTX_CHECK(c);
+  vfpi_status st;
+  if (A_vals) {
+    if ((st = set_values(c, c->d_row_ptr, nullptr, A_vals, false, 0)) != VFPI_OK) return st;
+  }
+  if (Jc) {
+    if ((st = set_contacts(c, Jc)) != VFPI_OK) return st;
+  }
+  if (b) {
+    const void* db;
+    VFPI_TRY_CUDA(device_view(c, b, c->esz * 3 * (size_t)c->N, 0, &db));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    VFPI_TRY_CUDA(DISPATCH(c, check_finite(db, 3 * (int64_t)c->N, c->d_err, c->stream)));
+    int flags = 0;
+    if ((st = read_err(c, &flags)) != VFPI_OK) return st;
+    if (flags) return arg_fail(c, VFPI_ERR_NONFINITE, "b has non-finite values");
+    VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, db, c->d_b)));
+  }
+  if (A_vals || Jc) {
+    if ((st = set_w(c)) != VFPI_OK) return st;
+  }
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_rhs(vfpi_t c, const void* b, const void* phi) {
+  CTX_CHECK(c);
+  if (b) {
+    const void* db;
+    VFPI_TRY_CUDA(device_view(c, b, c->esz * 3 * (size_t)c->N, 0, &db));
+    VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, db, c->d_b)));
+  }
+  if (phi && c->n_c > 0) {
+    const void* dp;
+    VFPI_TRY_CUDA(device_view(c, phi, c->esz * (size_t)c->n_c,
+                              round_up(c->esz * 3 * (size_t)c->N, 256), &dp));
+    VFPI_TRY_CUDA(DISPATCH(c, gather_phi(c, dp)));
+  }
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_velocity(vfpi_t c, const void* v) {
+  CTX_CHECK(c);
+  if (!v) return arg_fail(c, VFPI_ERR_INVALID_ARG, "v is NULL");
+  const void* dv;
+  VFPI_TRY_CUDA(device_view(c, v, c->esz * 3 * (size_t)c->N, 0, &dv));
+  VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dv, c->d_v0)));
+  return VFPI_OK;
+}
+
+static vfpi_status export_vec(vfpi_ctx* c, const void* internal, void* out) {
+  const size_t bytes = c->esz * 3 * (size_t)c->N;
+  void* dst;
+  VFPI_TRY_CUDA(out_view(c, out, bytes, 0, &dst));
+  VFPI_TRY_CUDA(DISPATCH(c, to_external(c, internal, dst)));
+  if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_velocity(vfpi_t c, void* v) {
+  CTX_CHECK(c);
+  if (!v) return arg_fail(c, VFPI_ERR_INVALID_ARG, "v is NULL");
+  return export_vec(c, c->d_v0, v);
+}
+
+vfpi_status vfpi_get_w(vfpi_t c, void* w) {
+  CTX_CHECK(c);
+  if (!w) return arg_fail(c, VFPI_ERR_INVALID_ARG, "w is NULL");
+  return export_vec(c, c->d_w, w);
+}
+
+vfpi_status vfpi_get_lambda(vfpi_t c, void* lambda) {
+  CTX_CHECK(c);
+  if (!lambda) return arg_fail(c, VFPI_ERR_INVALID_ARG, "lambda is NULL");
+  const size_t bytes = c->esz * 3 * (size_t)c->n_c;
+  if (bytes == 0) return VFPI_OK;
+  void* dst;
+  VFPI_TRY_CUDA(out_view(c, lambda, bytes, 0, &dst));
+  VFPI_TRY_CUDA(DISPATCH(c, lambda_external(c, dst)));
+  if (dst != lambda) VFPI_TRY_CUDA(to_caller(c, lambda, dst, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_status(vfpi_t c, int32_t* iters_out, double* theta_out) {
+  CTX_CHECK(c);
+  const int S = c->n_scenes;
+  std::vector<int32_t> it(S), stv(S);
+  std::vector<double> th(S);
+  int err = 0;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(it.data(), c->d_iters, 4 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(stv.data(), c->d_status, 4 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(th.data(), c->d_theta, 8 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  if (iters_out) std::memcpy(iters_out, it.data(), 4 * (size_t)S);
+  if (theta_out) std::memcpy(theta_out, th.data(), 8 * (size_t)S);
+  if (err & 1) return arg_fail(c, VFPI_ERR_TIMEOUT, "a grid barrier wait ran out; the iterate is invalid");
+  vfpi_status worst = VFPI_OK;
+  for (int q = 0; q < S; ++q) {
+    if (stv[q] == VFPI_ERR_NONFINITE) {
+      return arg_fail(c, VFPI_ERR_NONFINITE, "non-finite residual in scene " + std::to_string(q));
+    }
+    if (stv[q] == VFPI_NOT_CONVERGED) worst = VFPI_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+vfpi_status vfpi_solve_async(vfpi_t c) {
+  CTX_CHECK(c);
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th)));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_step(vfpi_t c, double* theta_out) {
+  CTX_CHECK(c);
+  // one sweep: l_max = 1, never "converged" early
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, 1, -1.0)));
+  if (!theta_out) return VFPI_OK;
+  std::vector<double> th(c->n_scenes);
+  vfpi_status st = vfpi_get_status(c, nullptr, th.data());
+  *theta_out = th[0];
+  if (c->n_scenes > 1)
+    for (int q = 0; q < c->n_scenes; ++q) theta_out[q] = th[q];
+  return st == VFPI_NOT_CONVERGED ? VFPI_OK : st;
+}
+
+vfpi_status vfpi_solve(vfpi_t c, void* v_inout, void* lambda_out, int32_t* iters_out, double* theta_out) {
+  CTX_CHECK(c);
+  vfpi_status st;
+  if (v_inout && (st = vfpi_set_velocity(c, v_inout)) != VFPI_OK) return st;
+  if ((st = vfpi_solve_async(c)) != VFPI_OK) return st;
+  vfpi_status run = vfpi_get_status(c, iters_out, theta_out);
+  if (run < 0) return run;
+  if (v_inout && (st = vfpi_get_velocity(c, v_inout)) != VFPI_OK) return st;
+  if (lambda_out && (st = vfpi_get_lambda(c, lambda_out)) != VFPI_OK) return st;
+  return run;
+}
+
+vfpi_status vfpi_integrate(vfpi_t c, double* x) {
+  CTX_CHECK(c);
+  if (!x) return arg_fail(c, VFPI_ERR_INVALID_ARG, "x is NULL");
+  const size_t bytes = 8 * 3 * (size_t)c->N;
+  if (on_device(x)) {
+    VFPI_TRY_CUDA(DISPATCH(c, integrate(c, x)));
+    return VFPI_OK;
+  }
+  const void* dx;
+  VFPI_TRY_CUDA(device_view(c, x, bytes, 0, &dx));
+  VFPI_TRY_CUDA(DISPATCH(c, integrate(c, const_cast<double*>(static_cast<const double*>(dx)))));
+  VFPI_TRY_CUDA(to_caller(c, x, dx, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_matvec(vfpi_t c, const void* x, void* y) {
+  CTX_CHECK(c);
+  if (!x || !y) return arg_fail(c, VFPI_ERR_INVALID_ARG, "x and y are required");
+  const void* dx;
+  VFPI_TRY_CUDA(device_view(c, x, c->esz * 3 * (size_t)c->N, 0, &dx));
+  VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dx, c->d_t0)));
+  VFPI_TRY_CUDA(DISPATCH(c, spmv(c, c->d_t0, c->d_t1)));
+  return export_vec(c, c->d_t1, y);
+}
+
+vfpi_status vfpi_last_kernel_ms(vfpi_t c, float* ms) {
+  CTX_CHECK(c);
+  if (!ms) return arg_fail(c, VFPI_ERR_INVALID_ARG, "ms is NULL");
+  if (!c->timed) return arg_fail(c, VFPI_ERR_INVALID_ARG, "no solve launched yet");
+  VFPI_TRY_CUDA(cudaEventSynchronize(c->ev1));
+  VFPI_TRY_CUDA(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_layout(vfpi_t c, int64_t* info) {
+  CTX_CHECK(c);
+  if (!info) return arg_fail(c, VFPI_ERR_INVALID_ARG, "info is NULL");
+  info[0] = c->n_pad;
+  info[1] = c->n_slices;
+  info[2] = 32 * c->n_entries;
+  info[3] = c->path;
+  info[4] = c->grid;
+  info[5] = c->nt;
+  return VFPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,699 @@
+// Device code of the V-FPI solver (sm_103a).
+//
+// Data layout (device, built once per A by the create path):
+//   * nodes are renumbered so that every scene starts on a multiple of 32 and
+//     32 consecutive internal rows form one "slice" (one warp, one lane per
+//     block row);
+//   * A is stored sliced-ELL: slice s holds len_s entries per lane (len_s = the
+//     longest block row of the slice; shorter rows are padded with zero blocks
+//     whose column is the slice's first row).  Entries are grouped in chunks of
+//     VW = 16 / sizeof(T) so that each lane reads one 128-bit vector per block
+//     component: chunk k of slice s stores the column indices as [32 lanes][VW]
+//     and the values as [9 components][32 lanes][VW]; the len_s % VW leftover
+//     entries follow as [32 lanes] and [9][32] scalars.  Every warp load is a
+//     fully used, contiguous 512-byte (or 128-byte) segment;
+//   * vectors (v, b, W) are one 16/32-byte Vec4 per node (x, y, z, pad).
+//
+// One sweep (Alg. 1 body) is fused into a single pass over the rows: the
+// block-row product r = A v - b (eq. pgd1), v* = v - W r, then -- for a node
+// carrying an S-contact -- the gather eta = R v* (eq. subp), the one-shot
+// strict solve (Alg. 2, eq. operator) with gamma = w_i (Prop. 3), and the
+// scatter v^{l+1} = v* + w_i R^T lambda (eq. vup); finally the FP64 partial of
+// ||v^{l+1} - v^l||^2.  D-contacts couple two rows and run in a second phase
+// after a barrier.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vfpi {
+
+// status values mirrored from vfpi.h (kept numeric to avoid a C++ dependency)
+constexpr int ST_OK = 0;
+constexpr int ST_NOT_CONVERGED = 1;
+constexpr int ST_NONFINITE = -2;
+constexpr int ST_TIMEOUT = -5;
+
+// bounded spin of the grid barrier: polls x sleep >= ~1 s before giving up
+constexpr long long kBarrierPolls = 1ll << 24;
+
+template <typename T>
+struct alignas(4 * sizeof(T)) Vec4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+struct DevProblem {
+  int32_t n_slices;
+  int32_t n_pad;                 // padded node count (n_slices * 32)
+  const int32_t* slice_len;      // [n_slices] entries per lane
+  const int64_t* slice_off;      // [n_slices] offset in entries (1 entry = 32 slots)
+  const T* vals;                 // sliced-ELL values
+  const int32_t* cols;           // sliced-ELL internal column indices
+  const Vec4<T>* b;              // [n_pad]
+  const Vec4<T>* w;              // [n_pad]
+  const int32_t* cslot;          // [n_pad] contact of the node or -1
+  int32_t n_c;
+  const int32_t* c_i;            // [n_c] internal node i
+  const int32_t* c_j;            // [n_c] internal node j or -1 (S-contact)
+  const T* c_R;                  // [9][n_c] plane-major rotation entries
+  const T* c_mu;                 // [n_c]
+  const T* c_phi;                // [n_c]
+  Vec4<T>* lam;                  // [n_c] lambda of the last sweep (n, t1, t2)
+  Vec4<T>* lam_star;             // [n_c] lambda* of the last sweep
+  const int32_t* d_list;         // D-contacts (internal contact ids)
+  Vec4<T>* v0;                   // ping-pong iterates
+  Vec4<T>* v1;
+};
+
+struct SolveCtl {
+  int32_t l_max;
+  double theta_th;
+  const double* norm_scale;      // [n_scenes] 1 or 1/sqrt(n_q)
+  double* partials;              // [2][grid] FP64 block partials (grid path)
+  unsigned int* bar;             // [2] barrier count, generation (grid path)
+  int32_t n_scenes;
+  const int32_t* order;          // [n_scenes] processing order (largest first)
+  const int32_t* scene_slice;    // [n_scenes+1]
+  const int32_t* scene_d;        // [n_scenes+1] range in d_list
+  int32_t* queue;                // scene work counter (CTA-per-scene path)
+  int32_t* iters;                // [n_scenes]
+  int32_t* status;               // [n_scenes]
+  double* theta;                 // [n_scenes]
+  int32_t n_d;                   // total D-contacts (grid path)
+  int* err;                      // bit 0: a barrier wait ran out
+};
+
+// ---------------------------------------------------------------------------
+// loads
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  static constexpr int VW = 4;
+  __device__ __forceinline__ static void vals(const float* p, float (&o)[4]) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  }
+  __device__ __forceinline__ static void cols(const int32_t* p, int (&o)[4]) {
+    const int4 q = __ldcs(reinterpret_cast<const int4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  }
+};
+template <>
+struct Chunk<double> {
+  static constexpr int VW = 2;
+  __device__ __forceinline__ static void vals(const double* p, double (&o)[2]) {
+    const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = q.x; o[1] = q.y;
+  }
+  __device__ __forceinline__ static void cols(const int32_t* p, int (&o)[2]) {
+    const int2 q = __ldcs(reinterpret_cast<const int2*>(p));
+    o[0] = q.x; o[1] = q.y;
+  }
+};
+
+__device__ __forceinline__ Vec4<float> ldv(const Vec4<float>* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return {q.x, q.y, q.z, q.w};
+}
+__device__ __forceinline__ Vec4<double> ldv(const Vec4<double>* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 c = reinterpret_cast<const double2*>(p)[1];
+  return {a.x, a.y, c.x, c.y};
+}
+__device__ __forceinline__ void stv(Vec4<float>* p, const Vec4<float>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ void stv(Vec4<double>* p, const Vec4<double>& v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+}
+
+// Position of entry e of lane `lane` in a slice with `len` entries at `off`.
+// Returns the column index position; *vpos gets the position of component 0
+// and *vstride the distance between components.
+template <typename T>
+__device__ __forceinline__ int64_t slot_pos(int64_t off, int len, int e, int lane, int64_t* vpos,
+                                            int* vstride) {
+  constexpr int VW = Chunk<T>::VW;
+  const int nfull = len / VW;
+  if (e < nfull * VW) {
+    const int k = e / VW, r = e % VW;
+    *vpos = off * 288 + (int64_t)k * (288 * VW) + lane * VW + r;
+    *vstride = 32 * VW;
+    return off * 32 + (int64_t)k * (32 * VW) + lane * VW + r;
+  }
+  const int t = e - nfull * VW;
+  *vpos = off * 288 + (int64_t)nfull * (288 * VW) + (int64_t)t * 288 + lane;
+  *vstride = 32;
+  return off * 32 + (int64_t)nfull * (32 * VW) + (int64_t)t * 32 + lane;
+}
+
+// ---------------------------------------------------------------------------
+// block-row product r = (A v)_row for one lane of a slice
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void row_product(const DevProblem<T>& P, int slice, int lane,
+                                            const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  const int len = P.slice_len[slice];
+  const int64_t off = P.slice_off[slice];
+  const T* __restrict__ vb = P.vals + off * 288;
+  const int32_t* __restrict__ cb = P.cols + off * 32;
+  a0 = T(0); a1 = T(0); a2 = T(0);
+  const int nfull = len / VW;
+#pragma unroll 1
+  for (int k = 0; k < nfull; ++k) {
+    int c[VW];
+    T m[9][VW];
+    Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
+    const T* p = vb + (int64_t)k * (288 * VW) + lane * VW;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Chunk<T>::vals(p + q * (32 * VW), m[q]);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const Vec4<T> x = ldv(vin + c[e]);
+      a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
+      a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
+      a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
+    }
+  }
+  const int ntail = len - nfull * VW;
+  const T* pt = vb + (int64_t)nfull * (288 * VW) + lane;
+  const int32_t* ct = cb + (int64_t)nfull * (32 * VW) + lane;
+  for (int t = 0; t < ntail; ++t) {
+    const int c = __ldcs(ct + t * 32);
+    T m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) m[q] = __ldcs(pt + t * 288 + q * 32);
+    const Vec4<T> x = ldv(vin + c);
+    a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
+    a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
+    a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one-shot contact solve (Alg. 2, strict operator of eq. operator)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct ContactRec {
+  T R[9];
+  T mu, phi;
+};
+
+template <typename T>
+__device__ __forceinline__ ContactRec<T> load_contact(const DevProblem<T>& P, int cs) {
+  ContactRec<T> c;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) c.R[q] = __ldg(P.c_R + (int64_t)q * P.n_c + cs);
+  c.mu = __ldg(P.c_mu + cs);
+  c.phi = __ldg(P.c_phi + cs);
+  return c;
+}
+
+// Given the relative surrogate velocity r = v*_i - v*_j (v*_i for an
+// S-contact) and gamma, compute lambda* and lambda.
+template <typename T>
+__device__ __forceinline__ void one_shot(const ContactRec<T>& c, T gamma, T rx, T ry, T rz,
+                                         Vec4<T>& ls, Vec4<T>& lam) {
+  // eta = R r  (eq. subp, J_{c,m} v*)
+  const T en = c.R[0] * rx + c.R[1] * ry + c.R[2] * rz;
+  const T e1 = c.R[3] * rx + c.R[4] * ry + c.R[5] * rz;
+  const T e2 = c.R[6] * rx + c.R[7] * ry + c.R[8] * rz;
+  // lambda* = -(gamma I)^{-1} (eta + phi e_n)   (Alg. 2)
+  ls.x = -(en + c.phi) / gamma;
+  ls.y = -e1 / gamma;
+  ls.z = -e2 / gamma;
+  ls.w = T(0);
+  // strict operator: normal clamp, then projection onto the disk mu*lambda_n
+  const T ln = ls.x > T(0) ? ls.x : T(0);
+  const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
+  const T rad = c.mu * ln;
+  const T s = (rho <= rad) ? T(1) : rad / rho;
+  lam.x = ln;
+  lam.y = s * ls.y;
+  lam.z = s * ls.z;
+  lam.w = T(0);
+}
+
+// R^T lambda
+template <typename T>
+__device__ __forceinline__ void rt_lambda(const ContactRec<T>& c, const Vec4<T>& l, T& dx, T& dy,
+                                          T& dz) {
+  dx = c.R[0] * l.x + c.R[3] * l.y + c.R[6] * l.z;
+  dy = c.R[1] * l.x + c.R[4] * l.y + c.R[7] * l.z;
+  dz = c.R[2] * l.x + c.R[5] * l.y + c.R[8] * l.z;
+}
+
+template <typename T>
+__device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
+  const double dx = (double)a.x - (double)b.x;
+  const double dy = (double)a.y - (double)b.y;
+  const double dz = (double)a.z - (double)b.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// One row of one sweep: returns this row's contribution to ||dv||^2 (0 for a
+// D-contact node, whose update happens in phase 2).
+template <typename T>
+__device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
+                                            const Vec4<T>* vin, Vec4<T>* vout) {
+  T a0, a1, a2;
+  row_product(P, slice, lane, vin, a0, a1, a2);
+  const int row = slice * 32 + lane;
+  const Vec4<T> vo = ldv(vin + row);
+  const Vec4<T> bb = ldv(P.b + row);
+  const Vec4<T> ww = ldv(P.w + row);
+  // eq. (pgd1): v* = v - W (A v - b)
+  Vec4<T> vn;
+  vn.x = vo.x - ww.x * (a0 - bb.x);
+  vn.y = vo.y - ww.y * (a1 - bb.y);
+  vn.z = vo.z - ww.z * (a2 - bb.z);
+  vn.w = T(0);
+  const int cs = __ldg(P.cslot + row);
+  if (cs >= 0) {
+    if (__ldg(P.c_j + cs) >= 0) {  // D-contact: finish in phase 2
+      stv(vout + row, vn);
+      return 0.0;
+    }
+    const ContactRec<T> c = load_contact(P, cs);
+    Vec4<T> ls, lam;
+    one_shot(c, ww.x, vn.x, vn.y, vn.z, ls, lam);   // gamma = w_i (Prop. 3)
+    T dx, dy, dz;
+    rt_lambda(c, lam, dx, dy, dz);
+    vn.x += ww.x * dx;                               // eq. (vup)
+    vn.y += ww.x * dy;
+    vn.z += ww.x * dz;
+    stv(P.lam + cs, lam);
+    stv(P.lam_star + cs, ls);
+  }
+  stv(vout + row, vn);
+  return sqdiff(vn, vo);
+}
+
+// Phase 2: D-contact d between internal nodes i and j (both rows hold v*).
+template <typename T>
+__device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, const Vec4<T>* vin,
+                                            Vec4<T>* vout) {
+  const int i = P.c_i[cs], j = P.c_j[cs];
+  const Vec4<T> si = ldv(vout + i), sj = ldv(vout + j);
+  const T wi = P.w[i].x, wj = P.w[j].x;
+  const ContactRec<T> c = load_contact(P, cs);
+  Vec4<T> ls, lam;
+  one_shot(c, wi + wj, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam);  // gamma = w_i + w_j
+  T dx, dy, dz;
+  rt_lambda(c, lam, dx, dy, dz);
+  Vec4<T> ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
+  Vec4<T> nj = {sj.x - wj * dx, sj.y - wj * dy, sj.z - wj * dz, T(0)};
+  stv(vout + i, ni);
+  stv(vout + j, nj);
+  stv(P.lam + cs, lam);
+  stv(P.lam_star + cs, ls);
+  return sqdiff(ni, ldv(vin + i)) + sqdiff(nj, ldv(vin + j));
+}
+
+// ---------------------------------------------------------------------------
+// reductions and the bounded grid barrier
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum over the block in a fixed order; every thread receives the result.
+template <int NT>
+__device__ __forceinline__ double block_allreduce(double x, double* red) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    double y = lane < NT / 32 ? red[lane] : 0.0;
+    y = warp_sum(y);
+    if (lane == 0) red[32] = y;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// All CTAs arrive; returns false if the wait ran out (the caller then stops).
+// Co-residency of all CTAs is guaranteed by the cooperative launch; the spin
+// is bounded anyway so that a fault elsewhere can never hang the GPU.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (ticket == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      ok = 0;
+      for (long long it = 0; it < kBarrierPolls; ++it) {
+        if (*vgen != gen) { ok = 1; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// solve kernels
+// ---------------------------------------------------------------------------
+
+// Grid-wide persistent solve of one scene: every warp owns slices
+// gw, gw + W, ...; one barrier per sweep (two with D-contacts).  theta is the
+// fixed-order sum of the per-CTA partials, computed identically by every CTA,
+// so all CTAs take the same stop decision without a further exchange.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
+  __shared__ double red[33];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (NT / 32);
+  int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+  double theta = 0.0;
+  for (;; ++l) {
+    const Vec4<T>* vin = cur ? P.v1 : P.v0;
+    Vec4<T>* vout = cur ? P.v0 : P.v1;
+    double acc = 0.0;
+    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row(P, s, lane, vin, vout);
+    if (ctl.n_d > 0) {
+      if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+      for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
+        acc += d_contact(P, P.d_list[d], vin, vout);
+    }
+    acc = block_allreduce<NT>(acc, red);
+    double* part = ctl.partials + (l & 1) * gridDim.x;
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+    double s2 = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += part[q];
+    s2 = block_allreduce<NT>(s2, red);
+    theta = sqrt(s2) * ctl.norm_scale[0];
+    cur ^= 1;
+    if (!isfinite(theta)) { st = ST_NONFINITE; break; }
+    if (theta < ctl.theta_th) { st = ST_OK; break; }
+    if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+  }
+  if (st != ST_TIMEOUT && cur == 1) {
+    // the latest iterate lives in v1: copy the rows this warp owns into v0
+    for (int s = gw; s < P.n_slices; s += nw) {
+      const int row = s * 32 + lane;
+      stv(P.v0 + row, ldv(P.v1 + row));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl.iters[0] = l;
+    ctl.theta[0] = theta;
+    ctl.status[0] = st;
+  }
+  if (st == ST_TIMEOUT && threadIdx.x == 0) atomicOr(ctl.err, 1);
+}
+
+// Persistent CTA-per-scene solve: CTAs pop scenes (largest first) from a
+// queue and run the whole V-FPI loop of a scene with block-level syncs only.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl ctl) {
+  __shared__ double red[33];
+  __shared__ int s_q;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(ctl.queue, 1);
+    __syncthreads();
+    const int q = s_q;
+    __syncthreads();
+    if (q >= ctl.n_scenes) break;
+    const int sc = ctl.order[q];
+    const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
+    const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
+    const double nscale = ctl.norm_scale[sc];
+    int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+    double theta = 0.0;
+    for (;; ++l) {
+      const Vec4<T>* vin = cur ? P.v1 : P.v0;
+      Vec4<T>* vout = cur ? P.v0 : P.v1;
+      double acc = 0.0;
+      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row(P, s, lane, vin, vout);
+      if (d1 > d0) {
+        __syncthreads();
+        for (int d = d0 + threadIdx.x; d < d1; d += NT) acc += d_contact(P, P.d_list[d], vin, vout);
+      }
+      theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
+      cur ^= 1;
+      if (!isfinite(theta)) { st = ST_NONFINITE; break; }
+      if (theta < ctl.theta_th) { st = ST_OK; break; }
+      if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+    }
+    if (cur == 1) {
+      for (int s = s0 + wid; s < s1; s += NT / 32) {
+        const int row = s * 32 + lane;
+        stv(P.v0 + row, ldv(P.v1 + row));
+      }
+    }
+    if (threadIdx.x == 0) {
+      ctl.iters[sc] = l;
+      ctl.theta[sc] = theta;
+      ctl.status[sc] = st;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// set-up and conversion kernels
+// ---------------------------------------------------------------------------
+
+// Validate the caller's BSR pattern: columns in range, strictly increasing,
+// diagonal present, no block across two scenes.  Error bits go to *err.
+static __global__ void k_validate_pattern(int N, const int32_t* __restrict__ row_ptr,
+                                          const int32_t* __restrict__ col_idx,
+                                          const int32_t* __restrict__ node_scene, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  if (r1 < r0) { atomicOr(err, 1); return; }
+  bool diag = false;
+  int prev = -1;
+  for (int p = r0; p < r1; ++p) {
+    const int c = col_idx[p];
+    if (c < 0 || c >= N) { atomicOr(err, 1); return; }
+    if (c <= prev) atomicOr(err, 2);
+    if (c == i) diag = true;
+    if (node_scene[c] != node_scene[i]) atomicOr(err, 4);
+    prev = c;
+  }
+  if (!diag) atomicOr(err, 16);
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ a, int64_t n, int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) atomicOr(err, 8);
+}
+
+// Fill every slot with a zero block pointing at its own row.
+static __global__ void k_fill_pad_cols(int n_slices, const int32_t* __restrict__ slice_len,
+                                       const int64_t* __restrict__ slice_off,
+                                       int32_t* __restrict__ cols) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_slices * 32) return;
+  const int s = row >> 5;
+  const int64_t base = slice_off[s] * 32;
+  const int n = slice_len[s] * 32;
+  // padding slots keep zero values; their column is the slice's first row
+  // (any valid row would do, one shared row makes the dead gathers a broadcast)
+  for (int k = row & 31; k < n; k += 32) cols[base + k] = s * 32;
+}
+
+// Scatter the caller's blocks into the sliced-ELL layout.
+template <typename T>
+__global__ void k_scatter_blocks(int N, const int32_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_idx, const T* __restrict__ vals,
+                                 const int32_t* __restrict__ node_map,
+                                 const int32_t* __restrict__ slice_len,
+                                 const int64_t* __restrict__ slice_off, int32_t* __restrict__ cols,
+                                 T* __restrict__ svals, int store_cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int p = node_map[i];
+  const int s = p >> 5, lane = p & 31;
+  const int len = slice_len[s];
+  const int64_t off = slice_off[s];
+  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  for (int e = 0; e < r1 - r0; ++e) {
+    int64_t vp;
+    int vs;
+    const int64_t cp = slot_pos<T>(off, len, e, lane, &vp, &vs);
+    if (store_cols) cols[cp] = node_map[col_idx[r0 + e]];
+    const T* src = vals + (int64_t)(r0 + e) * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) svals[vp + (int64_t)q * vs] = src[q];
+  }
+}
+
+// Per DOF: d = a_rr and s = ||A_r*||^2 in FP64 (Sec. IV.C), from the layout.
+template <typename T>
+__global__ void k_row_stats(DevProblem<T> P, double* __restrict__ ds) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= P.n_pad) return;
+  const int s = row >> 5, lane = row & 31;
+  const int len = P.slice_len[s];
+  const int64_t off = P.slice_off[s];
+  double d[3] = {0, 0, 0}, q2[3] = {0, 0, 0};
+  for (int e = 0; e < len; ++e) {
+    int64_t vp;
+    int vs;
+    const int64_t cp = slot_pos<T>(off, len, e, lane, &vp, &vs);
+    const int c = P.cols[cp];
+    T m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) m[q] = P.vals[vp + (int64_t)q * vs];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      q2[a] += (double)m[3 * a] * m[3 * a] + (double)m[3 * a + 1] * m[3 * a + 1] +
+               (double)m[3 * a + 2] * m[3 * a + 2];
+      if (c == row) d[a] += (double)m[4 * a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ds[6 * (int64_t)row + a] = d[a];
+    ds[6 * (int64_t)row + 3 + a] = q2[a];
+  }
+}
+
+// W from the row statistics: tied on contact nodes (both nodes of a D-contact
+// share one value), w_rr = a_rr / ||A_r*||^2 elsewhere (Sec. IV.C).
+template <typename T>
+__global__ void k_make_w_frobenius(int n_pad, const double* __restrict__ ds,
+                                   const int32_t* __restrict__ cslot, const int32_t* __restrict__ c_i,
+                                   const int32_t* __restrict__ c_j, Vec4<T>* __restrict__ w) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_pad) return;
+  const double* r = ds + 6 * (int64_t)row;
+  Vec4<T> o;
+  const int cs = cslot[row];
+  if (cs < 0) {
+    o.x = r[3] > 0 ? (T)(r[0] / r[3]) : T(0);
+    o.y = r[4] > 0 ? (T)(r[1] / r[4]) : T(0);
+    o.z = r[5] > 0 ? (T)(r[2] / r[5]) : T(0);
+  } else {
+    const int i = c_i[cs], j = c_j[cs];
+    const double* ri = ds + 6 * (int64_t)i;
+    double num = ri[0] + ri[1] + ri[2];
+    double den = ri[3] + ri[4] + ri[5];
+    if (j >= 0) {
+      const double* rj = ds + 6 * (int64_t)j;
+      num += rj[0] + rj[1] + rj[2];
+      den += rj[3] + rj[4] + rj[5];
+    }
+    const T wb = (T)(num / den);
+    o.x = o.y = o.z = wb;
+  }
+  o.w = T(0);
+  stv(w + row, o);
+}
+
+// W = alpha I (pad rows have A = 0 and b = 0, so they stay at v = 0 for any w)
+template <typename T>
+__global__ void k_w_scalar(int n_pad, T alpha, Vec4<T>* __restrict__ w) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_pad) return;
+  stv(w + row, Vec4<T>{alpha, alpha, alpha, T(0)});
+}
+
+// caller layout [3N] -> internal Vec4 rows
+template <typename T>
+__global__ void k_to_internal(int N, const T* __restrict__ ext, const int32_t* __restrict__ node_map,
+                              Vec4<T>* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  stv(out + node_map[i], Vec4<T>{ext[3 * (int64_t)i], ext[3 * (int64_t)i + 1],
+                                 ext[3 * (int64_t)i + 2], T(0)});
+}
+
+template <typename T>
+__global__ void k_to_external(int N, const Vec4<T>* __restrict__ in,
+                              const int32_t* __restrict__ node_map, T* __restrict__ ext) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const Vec4<T> v = ldv(in + node_map[i]);
+  ext[3 * (int64_t)i] = v.x;
+  ext[3 * (int64_t)i + 1] = v.y;
+  ext[3 * (int64_t)i + 2] = v.z;
+}
+
+// contact data in caller order -> internal (sorted) order
+template <typename T>
+__global__ void k_gather_contacts(int n_c, const int32_t* __restrict__ perm, const T* __restrict__ R,
+                                  const T* __restrict__ mu, const T* __restrict__ phi,
+                                  T* __restrict__ cR, T* __restrict__ cmu, T* __restrict__ cphi,
+                                  int write_R_mu) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_c) return;
+  const int e = perm[m];
+  if (write_R_mu) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) cR[(int64_t)q * n_c + m] = R[9 * (int64_t)e + q];
+    cmu[m] = mu[e];
+  }
+  if (phi) cphi[m] = phi[e];
+}
+
+template <typename T>
+__global__ void k_lambda_external(int n_c, const int32_t* __restrict__ perm,
+                                  const Vec4<T>* __restrict__ lam, T* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_c) return;
+  const Vec4<T> l = ldv(lam + m);
+  const int e = perm[m];
+  out[3 * (int64_t)e] = l.x;
+  out[3 * (int64_t)e + 1] = l.y;
+  out[3 * (int64_t)e + 2] = l.z;
+}
+
+// x_{k+1} = x_k + h v_hat in FP64 (eq. disc_dyn)
+template <typename T>
+__global__ void k_integrate(int N, double h, const Vec4<T>* __restrict__ v,
+                            const int32_t* __restrict__ node_map, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const Vec4<T> q = ldv(v + node_map[i]);
+  x[3 * (int64_t)i] += h * (double)q.x;
+  x[3 * (int64_t)i + 1] += h * (double)q.y;
+  x[3 * (int64_t)i + 2] += h * (double)q.z;
+}
+
+// y = A x on internal vectors
+template <typename T>
+__global__ void k_spmv(DevProblem<T> P, const Vec4<T>* __restrict__ x, Vec4<T>* __restrict__ y) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= P.n_slices) return;
+  T a0, a1, a2;
+  row_product(P, gw, lane, x, a0, a1, a2);
+  stv(y + gw * 32 + lane, Vec4<T>{a0, a1, a2, T(0)});
+}
+
+}  // namespace vfpi

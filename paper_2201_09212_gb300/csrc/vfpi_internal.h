@@ -1,0 +1,88 @@
+// Host-side internals of libvfpi: the context and the per-dtype launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vfpi.h"
+
+namespace vfpi {
+
+struct DevState;  // device pointers, see vfpi_ctx
+
+// Launchers, instantiated for float and double in vfpi_f32.cu / vfpi_f64.cu.
+template <typename T>
+struct Launch {
+  static cudaError_t validate_pattern(int N, const int32_t* row_ptr, const int32_t* col_idx,
+                                      const int32_t* node_scene, int* err, cudaStream_t s);
+  static cudaError_t check_finite(const void* a, int64_t n, int* err, cudaStream_t s);
+  static cudaError_t build_layout(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx,
+                                  const void* vals, bool store_cols);
+  static cudaError_t make_w(vfpi_ctx* c);
+  static cudaError_t to_internal(vfpi_ctx* c, const void* ext, void* internal);
+  static cudaError_t to_external(vfpi_ctx* c, const void* internal, void* ext);
+  static cudaError_t lambda_external(vfpi_ctx* c, void* out);
+  static cudaError_t gather_phi(vfpi_ctx* c, const void* phi_ext);
+  static cudaError_t integrate(vfpi_ctx* c, double* x_dev);
+  static cudaError_t spmv(vfpi_ctx* c, const void* x_int, void* y_int);
+  static cudaError_t solve(vfpi_ctx* c, int l_max, double theta_th);
+  static cudaError_t configure(vfpi_ctx* c);
+};
+
+}  // namespace vfpi
+
+// The opaque context behind vfpi_t.
+struct vfpi_ctx {
+  int dtype = VFPI_F32;
+  size_t esz = 4;
+  cudaStream_t stream = nullptr;
+  vfpi_opts opts{};
+  double h = 0.0;
+
+  // sizes
+  int N = 0, nnzb = 0, n_scenes = 1, n_slices = 0, n_pad = 0, n_c = 0, n_d = 0;
+  int64_t n_entries = 0;  // sum of slice lengths; stored block slots = 32 * n_entries
+
+  // host copies of the layout and contact bookkeeping
+  std::vector<int32_t> h_scene_ptr, h_scene_slice, h_node_map, h_slice_len, h_node_scene;
+  std::vector<int64_t> h_slice_off;
+  std::vector<int32_t> h_cperm;  // internal contact -> caller's index
+  std::vector<int32_t> h_ci, h_cj;
+
+  // device memory (owned)
+  int32_t *d_slice_len = nullptr;
+  int64_t* d_slice_off = nullptr;
+  void* d_vals = nullptr;
+  int32_t* d_cols = nullptr;
+  void *d_b = nullptr, *d_w = nullptr, *d_v0 = nullptr, *d_v1 = nullptr;
+  void *d_t0 = nullptr, *d_t1 = nullptr;    // internal temporaries (matvec)
+  int32_t* d_cslot = nullptr;
+  int32_t* d_node_map = nullptr;
+  int32_t* d_row_ptr = nullptr;             // caller's row pointers (value updates)
+  double* d_ds = nullptr;                   // per-DOF row statistics for W
+  int32_t *d_ci = nullptr, *d_cj = nullptr, *d_cperm = nullptr, *d_dlist = nullptr;
+  void *d_cR = nullptr, *d_cmu = nullptr, *d_cphi = nullptr;
+  void *d_lam = nullptr, *d_lam_star = nullptr;
+  int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
+  double* d_norm_scale = nullptr;
+  double* d_partials = nullptr;
+  unsigned int* d_bar = nullptr;
+  int* d_err = nullptr;
+  int32_t *d_iters = nullptr, *d_status = nullptr;
+  double* d_theta = nullptr;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+
+  // launch configuration
+  int path = 0;    // 1 grid-wide cooperative kernel, 2 CTA per scene
+  int grid = 0;    // CTAs
+  int nt = 0;      // threads per CTA
+  int max_grid = 0;
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  std::string err;
+};

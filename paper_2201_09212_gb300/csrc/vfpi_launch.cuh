@@ -1,0 +1,221 @@
+// Per-dtype launch wrappers (included by vfpi_f32.cu and vfpi_f64.cu only).
+#pragma once
+
+#include <algorithm>
+
+#include "vfpi_device.cuh"
+#include "vfpi_internal.h"
+
+namespace vfpi {
+
+inline int blocks_for(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
+
+template <typename T>
+DevProblem<T> dev_problem(vfpi_ctx* c) {
+  DevProblem<T> P;
+  P.n_slices = c->n_slices;
+  P.n_pad = c->n_pad;
+  P.slice_len = c->d_slice_len;
+  P.slice_off = c->d_slice_off;
+  P.vals = static_cast<const T*>(c->d_vals);
+  P.cols = c->d_cols;
+  P.b = static_cast<const Vec4<T>*>(c->d_b);
+  P.w = static_cast<const Vec4<T>*>(c->d_w);
+  P.cslot = c->d_cslot;
+  P.n_c = c->n_c;
+  P.c_i = c->d_ci;
+  P.c_j = c->d_cj;
+  P.c_R = static_cast<const T*>(c->d_cR);
+  P.c_mu = static_cast<const T*>(c->d_cmu);
+  P.c_phi = static_cast<const T*>(c->d_cphi);
+  P.lam = static_cast<Vec4<T>*>(c->d_lam);
+  P.lam_star = static_cast<Vec4<T>*>(c->d_lam_star);
+  P.d_list = c->d_dlist;
+  P.v0 = static_cast<Vec4<T>*>(c->d_v0);
+  P.v1 = static_cast<Vec4<T>*>(c->d_v1);
+  return P;
+}
+
+template <typename T>
+cudaError_t Launch<T>::validate_pattern(int N, const int32_t* row_ptr, const int32_t* col_idx,
+                                        const int32_t* node_scene, int* err, cudaStream_t s) {
+  if (N > 0) k_validate_pattern<<<blocks_for(N, 256), 256, 0, s>>>(N, row_ptr, col_idx, node_scene, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::check_finite(const void* a, int64_t n, int* err, cudaStream_t s) {
+  if (n > 0) {
+    const int blocks = (int)std::min<int64_t>(blocks_for(n, 256), 152 * 16);
+    k_check_finite<T><<<blocks, 256, 0, s>>>(static_cast<const T*>(a), n, err);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::build_layout(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx,
+                                    const void* vals, bool store_cols) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if (store_cols) {
+    if (c->n_slices > 0)
+      k_fill_pad_cols<<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
+          c->n_slices, c->d_slice_len, c->d_slice_off, c->d_cols);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemsetAsync(c->d_vals, 0, (size_t)c->n_entries * 288 * sizeof(T), s)) != cudaSuccess)
+    return e;
+  if (c->N > 0)
+    k_scatter_blocks<T><<<blocks_for(c->N, 128), 128, 0, s>>>(
+        c->N, row_ptr, col_idx, static_cast<const T*>(vals), c->d_node_map, c->d_slice_len,
+        c->d_slice_off, c->d_cols, static_cast<T*>(c->d_vals), store_cols ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::make_w(vfpi_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int np = c->n_pad;
+  if (np == 0) return cudaSuccess;
+  if (c->opts.w_mode == VFPI_W_FROBENIUS) {
+    k_row_stats<T><<<blocks_for(np, 128), 128, 0, s>>>(dev_problem<T>(c), c->d_ds);
+    k_make_w_frobenius<T><<<blocks_for(np, 256), 256, 0, s>>>(
+        np, c->d_ds, c->d_cslot, c->d_ci, c->d_cj, static_cast<Vec4<T>*>(c->d_w));
+  } else if (c->opts.w_mode == VFPI_W_SCALAR) {
+    k_w_scalar<T><<<blocks_for(np, 256), 256, 0, s>>>(np, (T)c->opts.alpha,
+                                                      static_cast<Vec4<T>*>(c->d_w));
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::to_internal(vfpi_ctx* c, const void* ext, void* internal) {
+  if (c->N > 0)
+    k_to_internal<T><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(
+        c->N, static_cast<const T*>(ext), c->d_node_map, static_cast<Vec4<T>*>(internal));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::to_external(vfpi_ctx* c, const void* internal, void* ext) {
+  if (c->N > 0)
+    k_to_external<T><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(
+        c->N, static_cast<const Vec4<T>*>(internal), c->d_node_map, static_cast<T*>(ext));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::lambda_external(vfpi_ctx* c, void* out) {
+  if (c->n_c > 0)
+    k_lambda_external<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
+        c->n_c, c->d_cperm, static_cast<const Vec4<T>*>(c->d_lam), static_cast<T*>(out));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::gather_phi(vfpi_ctx* c, const void* phi_ext) {
+  if (c->n_c > 0)
+    k_gather_contacts<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
+        c->n_c, c->d_cperm, nullptr, nullptr, static_cast<const T*>(phi_ext), nullptr, nullptr,
+        static_cast<T*>(c->d_cphi), 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::integrate(vfpi_ctx* c, double* x_dev) {
+  if (c->N > 0)
+    k_integrate<T><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(
+        c->N, c->h, static_cast<const Vec4<T>*>(c->d_v0), c->d_node_map, x_dev);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::spmv(vfpi_ctx* c, const void* x_int, void* y_int) {
+  if (c->n_slices > 0)
+    k_spmv<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, c->stream>>>(
+        dev_problem<T>(c), static_cast<const Vec4<T>*>(x_int), static_cast<Vec4<T>*>(y_int));
+  return cudaGetLastError();
+}
+
+// Kernel selection by threads per CTA.
+template <typename T, int NT>
+struct Kernels {
+  static void* grid() { return (void*)&k_solve_grid<T, NT>; }
+  static void* scenes() { return (void*)&k_solve_scenes<T, NT>; }
+};
+
+template <typename T>
+static void* pick_kernel(int path, int nt) {
+  switch (nt) {
+    case 64: return path == 1 ? Kernels<T, 64>::grid() : Kernels<T, 64>::scenes();
+    case 128: return path == 1 ? Kernels<T, 128>::grid() : Kernels<T, 128>::scenes();
+    case 256: return path == 1 ? Kernels<T, 256>::grid() : Kernels<T, 256>::scenes();
+    case 512: return path == 1 ? Kernels<T, 512>::grid() : Kernels<T, 512>::scenes();
+    default: return nullptr;
+  }
+}
+
+template <typename T>
+cudaError_t Launch<T>::configure(vfpi_ctx* c) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  void* k = pick_kernel<T>(c->path, c->nt);
+  if (!k) return cudaErrorInvalidValue;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c->nt, 0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  c->max_grid = per_sm * sms;
+  if (c->path == 1) {
+    // persistent grid: every CTA resident (cooperative launch), no more CTAs
+    // than there are warps' worth of slices
+    const int need = (c->n_slices + c->nt / 32 - 1) / (c->nt / 32);
+    c->grid = std::max(1, std::min(c->max_grid, need));
+  } else {
+    c->grid = std::max(1, std::min(c->max_grid, c->n_scenes));
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  SolveCtl ctl;
+  ctl.l_max = l_max;
+  ctl.theta_th = theta_th;
+  ctl.norm_scale = c->d_norm_scale;
+  ctl.partials = c->d_partials;
+  ctl.bar = c->d_bar;
+  ctl.n_scenes = c->n_scenes;
+  ctl.order = c->d_order;
+  ctl.scene_slice = c->d_scene_slice;
+  ctl.scene_d = c->d_scene_d;
+  ctl.queue = c->d_queue;
+  ctl.iters = c->d_iters;
+  ctl.status = c->d_status;
+  ctl.theta = c->d_theta;
+  ctl.n_d = c->n_d;
+  ctl.err = c->d_err;
+  // control words: barrier count/generation, error flag, scene queue
+  if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  DevProblem<T> P = dev_problem<T>(c);
+  void* args[] = {&P, &ctl};
+  void* k = pick_kernel<T>(c->path, c->nt);
+  if (!k) return cudaErrorInvalidValue;
+  if ((e = cudaEventRecord(c->ev0, s)) != cudaSuccess) return e;
+  if (c->path == 1)
+    e = cudaLaunchCooperativeKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
+  else
+    e = cudaLaunchKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
+  if (e != cudaSuccess) return e;
+  c->timed = true;
+  return cudaEventRecord(c->ev1, s);
+}
+
+}  // namespace vfpi
