@@ -176,6 +176,43 @@ vfpi_status vfpi_last_kernel_ms(vfpi_t ctx, float* ms);
  * scene), [4] CTAs of the solve launch, [5] threads per CTA. */
 vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info6);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free solve.  The paper has no counterpart to this entry point.
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory is owned by
+ * someone else's allocator or memory pool, plug-ins that may not touch the CUDA
+ * allocator, and loops that must never block on an allocation.  Everything
+ * above allocates device memory in vfpi_create; this call allocates nothing.
+ * It solves one small problem straight from the caller's buffers with
+ * W = the Frobenius choice (Sec. IV.C) and the strict operator, one CTA on the
+ * given stream, and returns the same iterate as vfpi_solve on that problem.
+ *
+ *  - FP32 only.  A, b, the contact arrays, v_in, v_out and lambda_out
+ *    (n_c * 3, caller's contact order) must be device memory; iters_out and
+ *    theta_out are host scalars (nullable).  The call synchronises the stream
+ *    to read them back.  Inputs are not re-validated beyond index ranges
+ *    (vfpi_create's checks do not run); out-of-range indices give
+ *    VFPI_ERR_INVALID_ARG.
+ *  - Limit: n_nodes <= VFPI_NOALLOC_MAX_NODES (4096, i.e. 12,288 DOF) and
+ *    n_c <= n_nodes; larger problems are rejected with VFPI_ERR_INVALID_ARG.
+ *  - Its scratch is a fixed array of about 0.4 MB in device memory, part of the
+ *    library image: every GPU that loads the library holds it until the
+ *    process exits.  The first call on a device looks up the array's device
+ *    address (with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share that one array, and it keeps the previous
+ *    call's contents (the call clears what must start empty).  Calls that
+ *    overlap on the GPU -- on different streams, or from different host
+ *    threads -- race on it; serialise them.
+ * ---------------------------------------------------------------------- */
+#define VFPI_NOALLOC_MAX_NODES 4096
+vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_contacts* Jc,
+                               double theta_th, int32_t l_max, int32_t residual_norm,
+                               const float* v_in, float* v_out, float* lambda_out,
+                               int32_t* iters_out, double* theta_out, void* cuda_stream);
+/* Message for the last failing vfpi_solve_noalloc call of this host thread. */
+const char* vfpi_noalloc_last_error(void);
+
 const char* vfpi_last_error(vfpi_t ctx);
 const char* vfpi_status_string(vfpi_status s);
 void vfpi_destroy(vfpi_t ctx);

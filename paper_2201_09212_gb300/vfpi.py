@@ -29,7 +29,8 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_velocity", "vfpi_get_velocity", "vfpi_get_lambda", "vfpi_get_w",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
-            "vfpi_last_error", "vfpi_status_string", "vfpi_destroy")
+            "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
+            "vfpi_noalloc_last_error")
 
 
 class VfpiError(RuntimeError):
@@ -93,6 +94,8 @@ def lib():
         "vfpi_last_error": (C.c_char_p, [vp]),
         "vfpi_status_string": (C.c_char_p, [st]),
         "vfpi_destroy": (None, [vp]),
+        "vfpi_solve_noalloc": (st, [vp, vp, vp, C.c_double, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "vfpi_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
