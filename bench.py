@@ -163,6 +163,114 @@ def run_reference(args, sc):
     print(json.dumps(line), flush=True)
 
 
+def batched_bench(args, torch, dev, stream, rank):
+    """4,096 independent uneven lattices (192-5,184 DOF each) on the ground plane,
+    one persistent CTA-per-scene launch per time step, the whole env step
+    (dynamics harness: b = M v + h M g - kappa (A - M)(x - x0), phi = z / h; warm
+    start; solve; x += h v_hat) captured in one CUDA graph.  Also times plain
+    per-scene solves of a sample of scenes on the same GPU for comparison."""
+    from paper_2201_09212_gb300 import scenes, vfpi
+    sc = scenes.lattice_batch(args.batch_scenes, seed=scenes.SEED_BASE + 4 + 1000 * rank)
+    meta = sc.meta
+    S = len(meta["sides"])
+    nq = meta["sides"].astype(np.int64) ** 3
+    dof_scene = np.repeat(np.arange(S), 3 * nq)
+    comp = np.tile(np.arange(3), int(nq.sum()))
+    h = sc.h
+    g_dof = meta["gravity"][dof_scene, comp]
+    kappa = (h * meta["k"] / meta["coef"])[dof_scene]
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+    s = vfpi.Solver.from_scene(sc, theta_th=THETA_TH, l_max=L_MAX, norm="rms", stream=stream)
+    x0 = T(sc.x0, np.float64)
+    x = x0.clone()
+    v = T(sc.v0, np.float32)
+    mass = T(sc.mass, np.float32)
+    hg = T(h * sc.mass * g_dof, np.float32)
+    kap = T(kappa, np.float32)
+    zi = T(3 * sc.node_i.astype(np.int64) + 2, np.int64)
+    Au = torch.empty_like(v)
+    b = torch.empty_like(v)
+    phi = torch.empty(sc.n_c, dtype=torch.float32, device=dev)
+
+    def env_step():
+        u = (x - x0).float()
+        s.matvec(u, out=Au)
+        torch.mul(mass, v, out=b)
+        b.add_(hg)
+        b.sub_(kap * (Au - mass * u))
+        torch.div(x.index_select(0, zi).float(), h, out=phi)
+        s.set_rhs(b, phi)
+        s.set_velocity(v)
+        s.solve_async()
+        s.integrate(x)
+        s.get_velocity(out=v)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            env_step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            env_step()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dof_iters, kms, its = 0, [], []
+        n_dof = 3 * nq
+        t_total = 0.0
+        for _ in range(args.batch_steps):
+            ev0.record(stream)
+            g.replay()
+            ev1.record(stream)
+            ev1.synchronize()
+            t_total += ev0.elapsed_time(ev1) / 1e3
+            it, _, _ = s.status()
+            its.append(it.copy())
+            dof_iters += int((n_dof * it).sum())
+            kms.append(s.last_kernel_ms())
+    its = np.array(its)
+    env_sps = S * args.batch_steps / t_total
+    bytes_scene = np.array([
+        algorithmic_bytes_per_sweep(type("Q", (), dict(n_nodes=int(n), n=3 * int(n), nnzb=int(bq), n_c=int(s_ ** 2)))())
+        for n, bq, s_ in zip(nq, np.diff(sc.row_ptr[sc.scene_ptr]), meta["sides"])])
+    alg = float((its * bytes_scene[None, :]).sum(axis=1).mean())
+    k_avg = float(np.mean(kms)) / 1e3
+    # plain per-scene solves (one context per scene) on a sample, same tolerance
+    rng = np.random.default_rng(0)
+    sample = rng.choice(S, size=min(args.per_scene_sample, S), replace=False)
+    per_ms = []
+    for q in sample:
+        n0, n1 = sc.scene_ptr[q], sc.scene_ptr[q + 1]
+        r0, r1 = sc.row_ptr[n0], sc.row_ptr[n1]
+        cm = (sc.node_i >= n0) & (sc.node_i < n1)
+        with vfpi.Solver(sc.row_ptr[n0:n1 + 1] - r0, sc.col_idx[r0:r1] - n0, sc.vals[r0:r1],
+                         sc.b[3 * n0:3 * n1], sc.node_i[cm] - n0, None, sc.R[cm], sc.mu[cm],
+                         sc.phi[cm], theta_th=THETA_TH, l_max=L_MAX, norm="rms",
+                         stream=stream) as s1:
+            s1.set_velocity(sc.v0[3 * n0:3 * n1])
+            for _ in range(2):
+                s1.solve_async()
+                s1.status()
+            per_ms.append(s1.last_kernel_ms())
+    per_scene_total = float(np.mean(per_ms)) / 1e3 * S
+    first_batch = kms[0] / 1e3
+    s.close()
+    return {
+        "workload": f"{S} lattices, side U{{4..12}}, {int(nq.sum()) * 3} DOF, {sc.nnzb} blocks, {sc.n_c} contacts",
+        "env_steps_per_s": env_sps, "ms_per_env_step": 1e3 * t_total / args.batch_steps,
+        "steps": args.batch_steps, "dof_iters_per_s": dof_iters / t_total,
+        "iters_per_scene": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
+        "solve_kernel": {"name": "k_solve_scenes<float,128>", "ms_avg": 1e3 * k_avg,
+                         "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0]},
+        "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
+        "per_scene_plain": {"sample": len(sample), "mean_solve_ms": float(np.mean(per_ms)),
+                            "extrapolated_all_scenes_s": per_scene_total,
+                            "batched_solve_s": first_batch,
+                            "speedup": per_scene_total / first_batch},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +280,10 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default="128,128,32")
+    ap.add_argument("--batch-scenes", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=30)
+    ap.add_argument("--per-scene-sample", type=int, default=32)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -265,6 +377,14 @@ def main():
     h2d = 4 * (sc.n + sc.n_c + sc.n) + 8 * sc.n
     d2h = 4 * (sc.n + 3 * sc.n_c) + 8 * sc.n
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_bench(args, torch, dev, stream, rank)
+        if dist:
+            t = torch.tensor([batched["ms_per_env_step"]], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            batched["env_steps_per_s"] = args.batch_scenes * ws * 1e3 / float(t.item())
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -300,6 +420,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
+        "batched": batched,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

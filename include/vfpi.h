@@ -137,8 +137,14 @@ vfpi_status vfpi_set_velocity(vfpi_t ctx, const void* v);
 /* Current iterate [3N] and the impulses of the last sweep [n_c * 3]. */
 vfpi_status vfpi_get_velocity(vfpi_t ctx, void* v);
 vfpi_status vfpi_get_lambda(vfpi_t ctx, void* lambda);
+/* lambda* = -(eta + phi e_n) / gamma of the last sweep [n_c * 3] (Alg. 2,
+ * before ProjectFC): it fixes the active set the adjoint differentiates at. */
+vfpi_status vfpi_get_lambda_star(vfpi_t ctx, void* lambda_star);
 /* The diagonal of W [3N] (Sec. IV.C). */
 vfpi_status vfpi_get_w(vfpi_t ctx, void* w);
+/* Per-step friction coefficients mu [n_c] (eq. scc) without re-validation;
+ * W does not depend on mu, so nothing else changes. */
+vfpi_status vfpi_set_friction(vfpi_t ctx, const void* mu);
 
 /* Exactly one V-FPI sweep (eq. pgd1, subp, Alg. 2, eq. vup) from the current
  * iterate; *theta_out (nullable, synchronises) gets ||v^{l+1} - v^l||. */
@@ -158,6 +164,21 @@ vfpi_status vfpi_solve_async(vfpi_t ctx);
 /* Synchronise and read the last solve's iteration counts and residuals
  * (arrays of n_scenes entries in batched mode; nullable). */
 vfpi_status vfpi_get_status(vfpi_t ctx, int32_t* iters_out, double* theta_out);
+
+/* Adjoint of the converged fixed point v = f(v; b, phi, mu) of Sec. IV,
+ * f(v) = v* + W J_c^T ProjectFC(lambda*(v*)), at the active set frozen by
+ * lambda_star [n_c * 3] (caller order; NULL = the last forward sweep's).
+ * With P' the Jacobian of the strict operator (Lemma 2 gives its slip part,
+ * ||d lambda_t / d lambda*_n|| = mu) and S = W J_c^T diag(P'_m / gamma_m) J_c,
+ * the adjoint g_bar solves (I - (I - S)(I - W A))^T g_bar = g_v; it is found by
+ * the transposed sweep iterated on u = W (I - S^T) g_bar -- the forward sweep
+ * with b := g_v and the contact step replaced by the frozen linear map
+ * u_i -= (w_i / gamma) R^T P'^T R (u*_i - u*_j) -- with the same theta_th and
+ * l_max as the forward solve.  Outputs (nullable): g_b = dL/db [3N] (= u at
+ * convergence), g_phi = dL/dphi [n_c] = -(P'^T z)_n / gamma and
+ * g_mu = dL/dmu [n_c] = lambda_n t . z_t (slip), z = J_c u*.  Synchronises. */
+vfpi_status vfpi_adjoint(vfpi_t ctx, const void* lambda_star, const void* g_v, void* g_b,
+                         void* g_phi, void* g_mu, int32_t* iters_out, double* theta_out);
 
 /* State update x_{k+1} = x_k + h v_hat (eq. disc_dyn) in FP64 on the device;
  * x_inout [3N] double. */

@@ -1,0 +1,135 @@
+"""PyTorch autograd for the V-FPI solve and checkpointed rollouts.
+
+``vfpi_solve(solver, b, phi, mu, v_warm)`` returns the converged ``v_hat`` of
+the solver's problem with right-hand side ``b``, penetration terms ``phi`` and
+friction ``mu``; its backward runs the library's adjoint kernel
+(``vfpi_adjoint``) at the active set of that forward solve (the forward saves
+its ``lambda*``), so it stays correct when a checkpointed segment is
+recomputed.  ``matvec(solver, x)`` is ``A x`` (backward ``A g``: the system
+matrix of the method is symmetric, Sec. II.A).
+
+``rollout`` integrates a rest-linearised lattice scene (or a batch of them)
+for ``steps`` time steps -- ``b_k = M v_k + h M g - kappa (A - M)(x_k - x_0)``,
+``phi_k = z_k / h`` on the ground contacts, ``v_{k+1} = v_hat_k``,
+``x_{k+1} = x_k + h v_hat_k`` -- recomputing every ``checkpoint`` steps in the
+backward pass instead of storing them.  The dynamics harness is plain tensor
+algebra; every solve and every product with A runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.utils.checkpoint as ckpt
+
+
+class _Solve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, solver, b, phi, mu, v_warm):
+        solver.set_rhs(b.detach().contiguous(), phi.detach().contiguous())
+        solver.set_friction(mu.detach().contiguous())
+        v = v_warm.detach().clone().contiguous()
+        solver.set_velocity(v)
+        solver.solve_async()
+        solver.get_velocity(out=v)
+        lam_star = torch.empty(3 * solver.n_c, dtype=b.dtype, device=b.device)
+        solver.get_lambda_star(out=lam_star)
+        _, _, st = solver.status()
+        ctx.solver = solver
+        ctx.save_for_backward(lam_star)
+        return v
+
+    @staticmethod
+    def backward(ctx, g_v):
+        (lam_star,) = ctx.saved_tensors
+        s = ctx.solver
+        g_b = torch.empty(s.n, dtype=g_v.dtype, device=g_v.device)
+        g_phi = torch.empty(s.n_c, dtype=g_v.dtype, device=g_v.device)
+        g_mu = torch.empty(s.n_c, dtype=g_v.dtype, device=g_v.device)
+        s.adjoint(g_v.contiguous(), lambda_star=lam_star, out_b=g_b, out_phi=g_phi, out_mu=g_mu)
+        return None, g_b, g_phi, g_mu, None
+
+
+class _Matvec(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, solver, x):
+        y = torch.empty_like(x)
+        solver.matvec(x.detach().contiguous(), out=y)
+        ctx.solver = solver
+        return y
+
+    @staticmethod
+    def backward(ctx, g):
+        y = torch.empty_like(g)
+        ctx.solver.matvec(g.contiguous(), out=y)
+        return None, y
+
+
+def vfpi_solve(solver, b, phi, mu, v_warm):
+    return _Solve.apply(solver, b, phi, mu, v_warm)
+
+
+def matvec(solver, x):
+    return _Matvec.apply(solver, x)
+
+
+class LatticeHarness:
+    """Per-DOF constants of rest-linearised lattice scenes (see module docstring)."""
+
+    def __init__(self, scene, device, dtype=torch.float32):
+        meta = scene.meta
+        h = scene.h
+        if meta.get("kind") == "lattice_batch":
+            nq = meta["sides"].astype(np.int64) ** 3
+            dof_scene = np.repeat(np.arange(len(nq)), 3 * nq)
+            g = meta["gravity"][dof_scene, np.tile(np.arange(3), int(nq.sum()))]
+            kappa = (h * meta["k"] / meta["coef"])[dof_scene]
+            self.scene_ptr = scene.scene_ptr
+        else:
+            coef = h * meta["c"] + h * h * meta["k"]
+            g = np.tile(np.asarray(meta["gravity"]), scene.n_nodes)
+            kappa = np.full(scene.n, h * meta["k"] / coef)
+            self.scene_ptr = np.array([0, scene.n_nodes], dtype=np.int32)
+        T = lambda a, dt=dtype: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        self.h = h
+        self.mass = T(scene.mass)
+        self.hg = T(h * scene.mass * g)
+        self.kappa = T(kappa)
+        self.x_rest = T(scene.x0, torch.float64)
+        self.zi = T(3 * scene.node_i.astype(np.int64) + 2, torch.int64)
+        self.dtype = dtype
+
+    def rhs(self, solver, x, v):
+        u = (x - self.x_rest).to(self.dtype)
+        b = self.mass * v + self.hg - self.kappa * (matvec(solver, u) - self.mass * u)
+        phi = x.index_select(0, self.zi).to(self.dtype) / self.h
+        return b, phi
+
+    def com_z(self, x):
+        """Height of each scene's centre of mass, [n_scenes]."""
+        z = x[2::3]
+        ptr = torch.as_tensor(self.scene_ptr, device=x.device, dtype=torch.int64)
+        counts = ptr[1:] - ptr[:-1]
+        idx = torch.repeat_interleave(torch.arange(len(counts), device=x.device), counts)
+        return torch.zeros(len(counts), dtype=x.dtype, device=x.device).index_add_(0, idx, z) / counts
+
+
+def rollout(solver, harness, x0, v0, mu, steps, checkpoint=8):
+    """Positions after ``steps`` time steps, differentiable in ``v0`` and ``mu``."""
+
+    def segment(x, v, mu_, n):
+        for _ in range(n):
+            b, phi = harness.rhs(solver, x, v)
+            v = vfpi_solve(solver, b, phi, mu_, v)
+            x = x + harness.h * v.to(x.dtype)
+        return x, v
+
+    x, v = x0, v0
+    k = 0
+    while k < steps:
+        n = min(checkpoint, steps - k)
+        if checkpoint and torch.is_grad_enabled():
+            x, v = ckpt.checkpoint(segment, x, v, mu, n, use_reentrant=False)
+        else:
+            x, v = segment(x, v, mu, n)
+        k += n
+    return x, v

@@ -123,7 +123,8 @@ void free_all(vfpi_ctx* c) {
                   c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi,
                   c->d_lam, c->d_lam_star, c->d_scene_slice, c->d_scene_d, c->d_order,
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
-                  c->d_status, c->d_theta, c->d_stage};
+                  c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
+                  c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -655,7 +656,7 @@ vfpi_status vfpi_set_rhs(vfpi_t c, const void* b, const void* phi) {
     const void* dp;
     VFPI_TRY_CUDA(device_view(c, phi, c->esz * (size_t)c->n_c,
                               round_up(c->esz * 3 * (size_t)c->N, 256), &dp));
-    VFPI_TRY_CUDA(DISPATCH(c, gather_phi(c, dp)));
+    VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, dp, c->d_cphi, false)));
   }
   return VFPI_OK;
 }
@@ -690,16 +691,88 @@ vfpi_status vfpi_get_w(vfpi_t c, void* w) {
   return export_vec(c, c->d_w, w);
 }
 
-vfpi_status vfpi_get_lambda(vfpi_t c, void* lambda) {
-  CTX_CHECK(c);
-  if (!lambda) return arg_fail(c, VFPI_ERR_INVALID_ARG, "lambda is NULL");
+static vfpi_status export_contact_vec(vfpi_ctx* c, const void* internal, void* out) {
+  if (!out) return arg_fail(c, VFPI_ERR_INVALID_ARG, "output is NULL");
   const size_t bytes = c->esz * 3 * (size_t)c->n_c;
   if (bytes == 0) return VFPI_OK;
   void* dst;
-  VFPI_TRY_CUDA(out_view(c, lambda, bytes, 0, &dst));
-  VFPI_TRY_CUDA(DISPATCH(c, lambda_external(c, dst)));
-  if (dst != lambda) VFPI_TRY_CUDA(to_caller(c, lambda, dst, bytes));
+  VFPI_TRY_CUDA(out_view(c, out, bytes, 0, &dst));
+  VFPI_TRY_CUDA(DISPATCH(c, lambda_external(c, internal, dst)));
+  if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
   return VFPI_OK;
+}
+
+vfpi_status vfpi_get_lambda(vfpi_t c, void* lambda) {
+  CTX_CHECK(c);
+  return export_contact_vec(c, c->d_lam, lambda);
+}
+
+vfpi_status vfpi_get_lambda_star(vfpi_t c, void* lambda_star) {
+  CTX_CHECK(c);
+  return export_contact_vec(c, c->d_lam_star, lambda_star);
+}
+
+vfpi_status vfpi_set_friction(vfpi_t c, const void* mu) {
+  CTX_CHECK(c);
+  if (!mu) return arg_fail(c, VFPI_ERR_INVALID_ARG, "mu is NULL");
+  if (c->n_c == 0) return VFPI_OK;
+  const void* dm;
+  VFPI_TRY_CUDA(device_view(c, mu, c->esz * (size_t)c->n_c, 0, &dm));
+  VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, dm, c->d_cmu, false)));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_adjoint(vfpi_t c, const void* lambda_star, const void* g_v, void* g_b,
+                         void* g_phi, void* g_mu, int32_t* iters_out, double* theta_out) {
+  CTX_CHECK(c);
+  if (!g_v) return arg_fail(c, VFPI_ERR_INVALID_ARG, "g_v is NULL");
+  const size_t vec = c->esz * 4 * (size_t)c->n_pad;
+  if (!c->d_adj_g) {
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_g, vec));
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_u0, vec));
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_u1, vec));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_adj_g, 0, vec, c->stream));
+  }
+  if (c->adj_nc != c->n_c) {
+    VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    for (void* p : {c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu})
+      if (p) cudaFree(p);
+    c->d_adj_ls = c->d_adj_gphi = c->d_adj_gmu = nullptr;
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_ls, c->esz * 4 * (size_t)c->n_c));
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_gphi, c->esz * (size_t)c->n_c));
+    VFPI_TRY_CUDA(dalloc(&c->d_adj_gmu, c->esz * (size_t)c->n_c));
+    c->adj_nc = c->n_c;
+  }
+  const size_t vb = c->esz * 3 * (size_t)c->N;
+  // frozen active set: the caller's lambda* or the last forward sweep's
+  if (lambda_star) {
+    const void* dl;
+    VFPI_TRY_CUDA(device_view(c, lambda_star, c->esz * 3 * (size_t)c->n_c, 0, &dl));
+    VFPI_TRY_CUDA(DISPATCH(c, contact_vec_internal(c, dl, c->d_adj_ls)));
+  } else if (c->n_c > 0) {
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_adj_ls, c->d_lam_star, c->esz * 4 * (size_t)c->n_c,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+  }
+  const void* dg;
+  VFPI_TRY_CUDA(device_view(c, g_v, vb, round_up(c->esz * 3 * (size_t)c->n_c, 256), &dg));
+  VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dg, c->d_adj_g)));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_adj_u0, 0, vec, c->stream));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_adj_u1, 0, vec, c->stream));
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, true)));
+  vfpi_status run = vfpi_get_status(c, iters_out, theta_out);
+  if (run < 0) return run;
+  vfpi_status st;
+  if (g_b && (st = export_vec(c, c->d_adj_u0, g_b)) != VFPI_OK) return st;
+  for (int k = 0; k < 2; ++k) {
+    void* out = k == 0 ? g_phi : g_mu;
+    if (!out || c->n_c == 0) continue;
+    const size_t bytes = c->esz * (size_t)c->n_c;
+    void* dst;
+    VFPI_TRY_CUDA(out_view(c, out, bytes, 0, &dst));
+    VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, k == 0 ? c->d_adj_gphi : c->d_adj_gmu, dst, true)));
+    if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
+  }
+  return run;
 }
 
 vfpi_status vfpi_get_status(vfpi_t c, int32_t* iters_out, double* theta_out) {
@@ -728,14 +801,14 @@ vfpi_status vfpi_get_status(vfpi_t c, int32_t* iters_out, double* theta_out) {
 
 vfpi_status vfpi_solve_async(vfpi_t c) {
   CTX_CHECK(c);
-  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th)));
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, false)));
   return VFPI_OK;
 }
 
 vfpi_status vfpi_step(vfpi_t c, double* theta_out) {
   CTX_CHECK(c);
   // one sweep: l_max = 1, never "converged" early
-  VFPI_TRY_CUDA(DISPATCH(c, solve(c, 1, -1.0)));
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, 1, -1.0, false)));
   if (!theta_out) return VFPI_OK;
   std::vector<double> th(c->n_scenes);
   vfpi_status st = vfpi_get_status(c, nullptr, th.data());

@@ -61,6 +61,9 @@ struct DevProblem {
   const T* c_phi;                // [n_c]
   Vec4<T>* lam;                  // [n_c] lambda of the last sweep (n, t1, t2)
   Vec4<T>* lam_star;             // [n_c] lambda* of the last sweep
+  const Vec4<T>* adj_ls;         // adjoint: frozen lambda* defining the active set
+  T* adj_gphi;                   // adjoint: dL/dphi [n_c] (internal order)
+  T* adj_gmu;                    // adjoint: dL/dmu  [n_c]
   const int32_t* d_list;         // D-contacts (internal contact ids)
   Vec4<T>* v0;                   // ping-pong iterates
   Vec4<T>* v1;
@@ -251,6 +254,38 @@ __device__ __forceinline__ void rt_lambda(const ContactRec<T>& c, const Vec4<T>&
   dz = c.R[2] * l.x + c.R[5] * l.y + c.R[8] * l.z;
 }
 
+// Adjoint of the contact step at a frozen active set.  With
+// S = W J^T P' Gamma^{-1} J (P' the Jacobian of the strict operator at the
+// frozen lambda*), the transpose iteration on u = W (I - S^T) g_bar reads
+// u_new = u* - (1/gamma) W J^T P'^T J u*; for one contact, z = R (u*_i - u*_j)
+// and q = P'^T z.  Returns q; also dL/dphi = -q_n / gamma and
+// dL/dmu = lambda_n t . z_t (slip only).
+template <typename T>
+__device__ __forceinline__ void adjoint_step(const ContactRec<T>& c, const Vec4<T>& ls, T gamma,
+                                             T rx, T ry, T rz, Vec4<T>& q, T& gphi, T& gmu) {
+  const T zn = c.R[0] * rx + c.R[1] * ry + c.R[2] * rz;
+  const T z1 = c.R[3] * rx + c.R[4] * ry + c.R[5] * rz;
+  const T z2 = c.R[6] * rx + c.R[7] * ry + c.R[8] * rz;
+  q = Vec4<T>{T(0), T(0), T(0), T(0)};
+  gmu = T(0);
+  const T ln = ls.x;
+  if (ln > T(0)) {
+    const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
+    if (rho <= c.mu * ln) {            // stick: P' = I
+      q.x = zn; q.y = z1; q.z = z2;
+    } else {                            // slip
+      const T t1 = ls.y / rho, t2 = ls.z / rho;
+      const T tz = t1 * z1 + t2 * z2;
+      const T kap = c.mu * ln / rho;
+      q.x = zn + c.mu * tz;
+      q.y = kap * (z1 - t1 * tz);
+      q.z = kap * (z2 - t2 * tz);
+      gmu = ln * tz;
+    }
+  }
+  gphi = -q.x / gamma;
+}
+
 template <typename T>
 __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
   const double dx = (double)a.x - (double)b.x;
@@ -260,8 +295,9 @@ __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
 }
 
 // One row of one sweep: returns this row's contribution to ||dv||^2 (0 for a
-// D-contact node, whose update happens in phase 2).
-template <typename T>
+// D-contact node, whose update happens in phase 2).  ADJ selects the adjoint
+// sweep (b is then dL/dv and the contact step is the frozen linear map).
+template <typename T, bool ADJ>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
                                             const Vec4<T>* vin, Vec4<T>* vout) {
   T a0, a1, a2;
@@ -283,38 +319,66 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
       return 0.0;
     }
     const ContactRec<T> c = load_contact(P, cs);
-    Vec4<T> ls, lam;
-    one_shot(c, ww.x, vn.x, vn.y, vn.z, ls, lam);   // gamma = w_i (Prop. 3)
-    T dx, dy, dz;
-    rt_lambda(c, lam, dx, dy, dz);
-    vn.x += ww.x * dx;                               // eq. (vup)
-    vn.y += ww.x * dy;
-    vn.z += ww.x * dz;
-    stv(P.lam + cs, lam);
-    stv(P.lam_star + cs, ls);
+    if constexpr (ADJ) {
+      Vec4<T> q;
+      T gphi, gmu;
+      adjoint_step(c, ldv(P.adj_ls + cs), ww.x, vn.x, vn.y, vn.z, q, gphi, gmu);
+      T dx, dy, dz;
+      rt_lambda(c, q, dx, dy, dz);
+      vn.x -= dx;                                    // (w_i / gamma) = 1
+      vn.y -= dy;
+      vn.z -= dz;
+      P.adj_gphi[cs] = gphi;
+      P.adj_gmu[cs] = gmu;
+    } else {
+      Vec4<T> ls, lam;
+      one_shot(c, ww.x, vn.x, vn.y, vn.z, ls, lam);   // gamma = w_i (Prop. 3)
+      T dx, dy, dz;
+      rt_lambda(c, lam, dx, dy, dz);
+      vn.x += ww.x * dx;                               // eq. (vup)
+      vn.y += ww.x * dy;
+      vn.z += ww.x * dz;
+      stv(P.lam + cs, lam);
+      stv(P.lam_star + cs, ls);
+    }
   }
   stv(vout + row, vn);
   return sqdiff(vn, vo);
 }
 
 // Phase 2: D-contact d between internal nodes i and j (both rows hold v*).
-template <typename T>
+template <typename T, bool ADJ>
 __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, const Vec4<T>* vin,
                                             Vec4<T>* vout) {
   const int i = P.c_i[cs], j = P.c_j[cs];
   const Vec4<T> si = ldv(vout + i), sj = ldv(vout + j);
   const T wi = P.w[i].x, wj = P.w[j].x;
   const ContactRec<T> c = load_contact(P, cs);
-  Vec4<T> ls, lam;
-  one_shot(c, wi + wj, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam);  // gamma = w_i + w_j
-  T dx, dy, dz;
-  rt_lambda(c, lam, dx, dy, dz);
-  Vec4<T> ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
-  Vec4<T> nj = {sj.x - wj * dx, sj.y - wj * dy, sj.z - wj * dz, T(0)};
+  const T gamma = wi + wj;                                 // eq. (diagonal), D-contact
+  Vec4<T> ni, nj;
+  if constexpr (ADJ) {
+    Vec4<T> q;
+    T gphi, gmu;
+    adjoint_step(c, ldv(P.adj_ls + cs), gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, q, gphi, gmu);
+    T dx, dy, dz;
+    rt_lambda(c, q, dx, dy, dz);
+    const T fi = wi / gamma, fj = wj / gamma;
+    ni = {si.x - fi * dx, si.y - fi * dy, si.z - fi * dz, T(0)};
+    nj = {sj.x + fj * dx, sj.y + fj * dy, sj.z + fj * dz, T(0)};
+    P.adj_gphi[cs] = gphi;
+    P.adj_gmu[cs] = gmu;
+  } else {
+    Vec4<T> ls, lam;
+    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam);
+    T dx, dy, dz;
+    rt_lambda(c, lam, dx, dy, dz);
+    ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
+    nj = {sj.x - wj * dx, sj.y - wj * dy, sj.z - wj * dz, T(0)};
+    stv(P.lam + cs, lam);
+    stv(P.lam_star + cs, ls);
+  }
   stv(vout + i, ni);
   stv(vout + j, nj);
-  stv(P.lam + cs, lam);
-  stv(P.lam_star + cs, ls);
   return sqdiff(ni, ldv(vin + i)) + sqdiff(nj, ldv(vin + j));
 }
 
@@ -382,7 +446,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
 // gw, gw + W, ...; one barrier per sweep (two with D-contacts).  theta is the
 // fixed-order sum of the per-CTA partials, computed identically by every CTA,
 // so all CTAs take the same stop decision without a further exchange.
-template <typename T, int NT>
+template <typename T, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[33];
   __shared__ int s_ok;
@@ -395,11 +459,11 @@ __global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     double acc = 0.0;
-    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row(P, s, lane, vin, vout);
+    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout);
     if (ctl.n_d > 0) {
       if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
       for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
-        acc += d_contact(P, P.d_list[d], vin, vout);
+        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout);
     }
     acc = block_allreduce<NT>(acc, red);
     double* part = ctl.partials + (l & 1) * gridDim.x;
@@ -431,7 +495,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl
 
 // Persistent CTA-per-scene solve: CTAs pop scenes (largest first) from a
 // queue and run the whole V-FPI loop of a scene with block-level syncs only.
-template <typename T, int NT>
+template <typename T, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[33];
   __shared__ int s_q;
@@ -453,10 +517,11 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
       const Vec4<T>* vin = cur ? P.v1 : P.v0;
       Vec4<T>* vout = cur ? P.v0 : P.v1;
       double acc = 0.0;
-      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row(P, s, lane, vin, vout);
+      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout);
       if (d1 > d0) {
         __syncthreads();
-        for (int d = d0 + threadIdx.x; d < d1; d += NT) acc += d_contact(P, P.d_list[d], vin, vout);
+        for (int d = d0 + threadIdx.x; d < d1; d += NT)
+          acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout);
       }
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;
@@ -671,6 +736,26 @@ __global__ void k_lambda_external(int n_c, const int32_t* __restrict__ perm,
   out[3 * (int64_t)e] = l.x;
   out[3 * (int64_t)e + 1] = l.y;
   out[3 * (int64_t)e + 2] = l.z;
+}
+
+// per-contact 3-vectors in caller order -> internal Vec4 (contact m takes caller's perm[m])
+template <typename T>
+__global__ void k_contact_vec_internal(int n_c, const int32_t* __restrict__ perm,
+                                       const T* __restrict__ ext, Vec4<T>* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_c) return;
+  const int e = perm[m];
+  stv(out + m, Vec4<T>{ext[3 * (int64_t)e], ext[3 * (int64_t)e + 1], ext[3 * (int64_t)e + 2], T(0)});
+}
+
+// per-contact scalars: internal -> caller order, or caller -> internal
+template <typename T>
+__global__ void k_contact_scalar(int n_c, const int32_t* __restrict__ perm, const T* __restrict__ in,
+                                 T* __restrict__ out, int to_external) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_c) return;
+  if (to_external) out[perm[m]] = in[m];
+  else out[m] = in[perm[m]];
 }
 
 // x_{k+1} = x_k + h v_hat in FP64 (eq. disc_dyn)

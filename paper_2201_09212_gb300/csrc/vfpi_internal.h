@@ -24,11 +24,12 @@ struct Launch {
   static cudaError_t make_w(vfpi_ctx* c);
   static cudaError_t to_internal(vfpi_ctx* c, const void* ext, void* internal);
   static cudaError_t to_external(vfpi_ctx* c, const void* internal, void* ext);
-  static cudaError_t lambda_external(vfpi_ctx* c, void* out);
-  static cudaError_t gather_phi(vfpi_ctx* c, const void* phi_ext);
+  static cudaError_t lambda_external(vfpi_ctx* c, const void* lam_int, void* out);
+  static cudaError_t contact_vec_internal(vfpi_ctx* c, const void* ext, void* out);
+  static cudaError_t contact_scalar(vfpi_ctx* c, const void* in, void* out, bool to_external);
   static cudaError_t integrate(vfpi_ctx* c, double* x_dev);
   static cudaError_t spmv(vfpi_ctx* c, const void* x_int, void* y_int);
-  static cudaError_t solve(vfpi_ctx* c, int l_max, double theta_th);
+  static cudaError_t solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoint);
   static cudaError_t configure(vfpi_ctx* c);
 };
 
@@ -73,6 +74,10 @@ struct vfpi_ctx {
   int* d_err = nullptr;
   int32_t *d_iters = nullptr, *d_status = nullptr;
   double* d_theta = nullptr;
+  // adjoint (allocated on first use): rhs dL/dv, iterates, frozen lambda*, outputs
+  void *d_adj_g = nullptr, *d_adj_u0 = nullptr, *d_adj_u1 = nullptr, *d_adj_ls = nullptr;
+  void *d_adj_gphi = nullptr, *d_adj_gmu = nullptr;
+  int adj_nc = -1;
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
 

@@ -11,7 +11,7 @@ namespace vfpi {
 inline int blocks_for(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
 
 template <typename T>
-DevProblem<T> dev_problem(vfpi_ctx* c) {
+DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   DevProblem<T> P;
   P.n_slices = c->n_slices;
   P.n_pad = c->n_pad;
@@ -33,6 +33,14 @@ DevProblem<T> dev_problem(vfpi_ctx* c) {
   P.d_list = c->d_dlist;
   P.v0 = static_cast<Vec4<T>*>(c->d_v0);
   P.v1 = static_cast<Vec4<T>*>(c->d_v1);
+  P.adj_ls = static_cast<const Vec4<T>*>(c->d_adj_ls);
+  P.adj_gphi = static_cast<T*>(c->d_adj_gphi);
+  P.adj_gmu = static_cast<T*>(c->d_adj_gmu);
+  if (adjoint) {
+    P.b = static_cast<const Vec4<T>*>(c->d_adj_g);
+    P.v0 = static_cast<Vec4<T>*>(c->d_adj_u0);
+    P.v1 = static_cast<Vec4<T>*>(c->d_adj_u1);
+  }
   return P;
 }
 
@@ -105,19 +113,26 @@ cudaError_t Launch<T>::to_external(vfpi_ctx* c, const void* internal, void* ext)
 }
 
 template <typename T>
-cudaError_t Launch<T>::lambda_external(vfpi_ctx* c, void* out) {
+cudaError_t Launch<T>::lambda_external(vfpi_ctx* c, const void* lam_int, void* out) {
   if (c->n_c > 0)
     k_lambda_external<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
-        c->n_c, c->d_cperm, static_cast<const Vec4<T>*>(c->d_lam), static_cast<T*>(out));
+        c->n_c, c->d_cperm, static_cast<const Vec4<T>*>(lam_int), static_cast<T*>(out));
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::gather_phi(vfpi_ctx* c, const void* phi_ext) {
+cudaError_t Launch<T>::contact_vec_internal(vfpi_ctx* c, const void* ext, void* out) {
   if (c->n_c > 0)
-    k_gather_contacts<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
-        c->n_c, c->d_cperm, nullptr, nullptr, static_cast<const T*>(phi_ext), nullptr, nullptr,
-        static_cast<T*>(c->d_cphi), 0);
+    k_contact_vec_internal<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
+        c->n_c, c->d_cperm, static_cast<const T*>(ext), static_cast<Vec4<T>*>(out));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::contact_scalar(vfpi_ctx* c, const void* in, void* out, bool to_external) {
+  if (c->n_c > 0)
+    k_contact_scalar<T><<<blocks_for(c->n_c, 256), 256, 0, c->stream>>>(
+        c->n_c, c->d_cperm, static_cast<const T*>(in), static_cast<T*>(out), to_external ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -137,20 +152,22 @@ cudaError_t Launch<T>::spmv(vfpi_ctx* c, const void* x_int, void* y_int) {
   return cudaGetLastError();
 }
 
-// Kernel selection by threads per CTA.
+// Kernel selection by threads per CTA and mode.
 template <typename T, int NT>
 struct Kernels {
-  static void* grid() { return (void*)&k_solve_grid<T, NT>; }
-  static void* scenes() { return (void*)&k_solve_scenes<T, NT>; }
+  static void* get(int path, bool adj) {
+    if (path == 1) return adj ? (void*)&k_solve_grid<T, NT, true> : (void*)&k_solve_grid<T, NT, false>;
+    return adj ? (void*)&k_solve_scenes<T, NT, true> : (void*)&k_solve_scenes<T, NT, false>;
+  }
 };
 
 template <typename T>
-static void* pick_kernel(int path, int nt) {
+static void* pick_kernel(int path, int nt, bool adj = false) {
   switch (nt) {
-    case 64: return path == 1 ? Kernels<T, 64>::grid() : Kernels<T, 64>::scenes();
-    case 128: return path == 1 ? Kernels<T, 128>::grid() : Kernels<T, 128>::scenes();
-    case 256: return path == 1 ? Kernels<T, 256>::grid() : Kernels<T, 256>::scenes();
-    case 512: return path == 1 ? Kernels<T, 512>::grid() : Kernels<T, 512>::scenes();
+    case 64: return Kernels<T, 64>::get(path, adj);
+    case 128: return Kernels<T, 128>::get(path, adj);
+    case 256: return Kernels<T, 256>::get(path, adj);
+    case 512: return Kernels<T, 512>::get(path, adj);
     default: return nullptr;
   }
 }
@@ -162,11 +179,14 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  void* k = pick_kernel<T>(c->path, c->nt);
-  if (!k) return cudaErrorInvalidValue;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c->nt, 0)) != cudaSuccess)
-    return e;
+  for (int adj = 0; adj < 2; ++adj) {  // one grid fits both modes
+    void* k = pick_kernel<T>(c->path, c->nt, adj != 0);
+    if (!k) return cudaErrorInvalidValue;
+    int q = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, 0)) != cudaSuccess) return e;
+    per_sm = adj ? std::min(per_sm, q) : q;
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   c->max_grid = per_sm * sms;
   if (c->path == 1) {
@@ -181,7 +201,7 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th) {
+cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoint) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   SolveCtl ctl;
@@ -204,18 +224,22 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th) {
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  DevProblem<T> P = dev_problem<T>(c);
+  DevProblem<T> P = dev_problem<T>(c, adjoint);
   void* args[] = {&P, &ctl};
-  void* k = pick_kernel<T>(c->path, c->nt);
+  void* k = pick_kernel<T>(c->path, c->nt, adjoint);
   if (!k) return cudaErrorInvalidValue;
-  if ((e = cudaEventRecord(c->ev0, s)) != cudaSuccess) return e;
+  // inside a stream capture the events become graph nodes that record on replay
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
+  const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  if ((e = cudaEventRecordWithFlags(c->ev0, s, flags)) != cudaSuccess) return e;
   if (c->path == 1)
     e = cudaLaunchCooperativeKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
   else
     e = cudaLaunchKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
   if (e != cudaSuccess) return e;
   c->timed = true;
-  return cudaEventRecord(c->ev1, s);
+  return cudaEventRecordWithFlags(c->ev1, s, flags);
 }
 
 }  // namespace vfpi

@@ -398,8 +398,10 @@ def concat_scenes(scenes, dtype=None) -> Scene:
         vals=np.concatenate([s.vals for s in scenes]).astype(dtype), b=cat("b"),
         node_i=node_i.astype(np.int32), node_j=node_j.astype(np.int32), R=cat("R"),
         mu=cat("mu"), phi=cat("phi"), v0=cat("v0"), h=scenes[0].h,
-        x0=np.concatenate([s.x0 for s in scenes]),
-        mass=np.concatenate([s.mass for s in scenes]),
+        x0=(np.concatenate([s.x0 for s in scenes])
+            if all(s.x0 is not None for s in scenes) else None),
+        mass=(np.concatenate([s.mass for s in scenes])
+              if all(s.mass is not None for s in scenes) else None),
         scene_ptr=node_off.astype(np.int32),
         meta=dict(kind="batch", n_scenes=len(scenes)))
 
@@ -478,3 +480,79 @@ def random_problem(rng, n_nodes, n_contacts, *, density=0.3, d_contacts=0,
         mu=rng.uniform(*mu_range, size=m).astype(dtype),
         phi=(phi_scale * rng.standard_normal(m)).astype(dtype), v0=v0.astype(dtype),
         meta=dict(kind="random"))
+
+
+def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-3,
+                  k_scale_range=(0.5, 2.0), mu_range=(0.2, 0.8), v_down=0.1, v_sigma=1e-3,
+                  spacing=0.01, dtype=np.float32) -> Scene:
+    """``n_scenes`` independent rest-linearized cubic lattices on the ground plane,
+    concatenated into one batched problem (vectorised; same physics as
+    :func:`batched_lattices`).
+
+    A rest lattice has ``A = M + (h c + h^2 k) L`` with ``L = sum d d^T`` over
+    its springs, so every scene of side s reuses one ``L_s`` scaled by its own
+    stiffness.  Per scene: side ``U{side_range}``, ``k = 1e3 * U[k_scale_range]``,
+    gravity tilted by U[0, 30] degrees, friction ``mu ~ U[mu_range]`` per contact;
+    bottom layer on ``z = 0`` (phi = 0).  ``meta`` carries per-scene arrays
+    (side, k, coef = h c + h^2 k, gravity) for dynamics harnesses.
+    """
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_range[0], side_range[1] + 1, size=n_scenes)
+    kk = 1e3 * rng.uniform(*k_scale_range, size=n_scenes)
+    grav = np.array([tilted_gravity(rng) for _ in range(n_scenes)])
+    coef = h * c + h * h * kk
+    tmpl = {}
+    for s in np.unique(sides):
+        s = int(s)
+        ix, iy, iz = _grid_index(s, s, s)
+        x = np.stack([ix, iy, iz], axis=1) * spacing
+        rp, col, L, _ = lattice_system(s, s, s, x, x, np.zeros((s ** 3, 3)), mass=0.0, k=1.0,
+                                       c=0.0, h=1.0, gravity=(0, 0, 0), dtype=np.float64)
+        diag = np.nonzero(col == np.repeat(np.arange(s ** 3), np.diff(rp)))[0]
+        tmpl[s] = (rp, col, L.astype(np.float64), diag, x)
+    N_q = sides ** 3
+    node_off = np.zeros(n_scenes + 1, dtype=np.int64)
+    node_off[1:] = np.cumsum(N_q)
+    nnzb_q = np.array([tmpl[int(s)][1].shape[0] for s in sides])
+    blk_off = np.zeros(n_scenes + 1, dtype=np.int64)
+    blk_off[1:] = np.cumsum(nnzb_q)
+    N, nnzb = int(node_off[-1]), int(blk_off[-1])
+    row_ptr = np.empty(N + 1, dtype=np.int64)
+    col = np.empty(nnzb, dtype=np.int32)
+    vals = np.empty((nnzb, 3, 3), dtype=dtype)
+    x0 = np.empty((N, 3))
+    eye = np.eye(3)
+    for s in np.unique(sides):
+        s = int(s)
+        rp, cl, L, diag, xs = tmpl[s]
+        qs = np.nonzero(sides == s)[0]
+        for q in qs:
+            n0, b0 = node_off[q], blk_off[q]
+            row_ptr[n0:n0 + s ** 3] = rp[:-1] + b0
+            col[b0:b0 + cl.shape[0]] = cl + n0
+            x0[n0:n0 + s ** 3] = xs
+        # values of the whole group at once: coef_q * L + M on the diagonal blocks
+        blk = coef[qs][:, None, None, None] * L[None]
+        blk[:, diag] += mass * eye
+        for r, q in enumerate(qs):
+            b0 = blk_off[q]
+            vals[b0:b0 + L.shape[0]] = blk[r].astype(dtype)
+    row_ptr[N] = nnzb
+    v = np.zeros((N, 3))
+    v[:, 2] = -v_down
+    v += rng.normal(0.0, v_sigma, size=(N, 3))
+    scene_of = np.repeat(np.arange(n_scenes), N_q)
+    g_node = grav[scene_of]
+    b = (mass * v + h * mass * g_node).ravel()
+    bottom = np.concatenate([node_off[q] + np.arange(int(sides[q]) ** 2) for q in range(n_scenes)])
+    n_c = bottom.shape[0]
+    R = contact_frames(np.tile([0.0, 0.0, 1.0], (n_c, 1)))
+    return Scene(
+        n_nodes=N, row_ptr=row_ptr.astype(np.int32), col_idx=col, vals=vals,
+        b=b.astype(dtype), node_i=bottom.astype(np.int32),
+        node_j=np.full(n_c, -1, dtype=np.int32), R=R.astype(dtype),
+        mu=rng.uniform(*mu_range, size=n_c).astype(dtype), phi=np.zeros(n_c, dtype=dtype),
+        v0=v.ravel().astype(dtype), h=h, x0=x0.ravel(), mass=np.full(3 * N, mass),
+        scene_ptr=node_off.astype(np.int32),
+        meta=dict(kind="lattice_batch", sides=sides, k=kk, coef=coef, gravity=grav,
+                  node_mass=mass, seed=seed))

@@ -28,6 +28,7 @@ NORMS = {"abs": 0, "rms": 1}
 EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_velocity", "vfpi_get_velocity", "vfpi_get_lambda", "vfpi_get_w",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
+            "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
             "vfpi_noalloc_last_error")
@@ -83,6 +84,9 @@ def lib():
         "vfpi_get_velocity": (st, [vp, vp]),
         "vfpi_get_lambda": (st, [vp, vp]),
         "vfpi_get_w": (st, [vp, vp]),
+        "vfpi_get_lambda_star": (st, [vp, vp]),
+        "vfpi_set_friction": (st, [vp, vp]),
+        "vfpi_adjoint": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "vfpi_step": (st, [vp, vp]),
         "vfpi_solve": (st, [vp, vp, vp, vp, vp]),
         "vfpi_solve_async": (st, [vp]),
@@ -285,6 +289,34 @@ class Solver:
         k = _Keep()
         self._check(self._L.vfpi_get_lambda(self._h, k.ptr(out, self.np_dtype)))
         return out
+
+    def get_lambda_star(self, out=None):
+        out = self._out(3 * self.n_c, out)
+        k = _Keep()
+        self._check(self._L.vfpi_get_lambda_star(self._h, k.ptr(out, self.np_dtype)))
+        return out
+
+    def set_friction(self, mu):
+        k = _Keep()
+        self._check(self._L.vfpi_set_friction(self._h, k.ptr(mu, self.np_dtype)))
+
+    def adjoint(self, g_v, lambda_star=None, out_b=None, out_phi=None, out_mu=None):
+        """Implicit adjoint of the converged solve: returns (dL/db, dL/dphi, dL/dmu,
+        iters, theta) for dL/dv = g_v at the active set frozen by ``lambda_star``."""
+        k = _Keep()
+        g_b = self._out(self.n, out_b)
+        g_phi = self._out(self.n_c, out_phi)
+        g_mu = self._out(self.n_c, out_mu)
+        iters = np.zeros(self.n_scenes, dtype=np.int32)
+        theta = np.zeros(self.n_scenes, dtype=np.float64)
+        st = self._L.vfpi_adjoint(self._h, k.ptr(lambda_star, self.np_dtype),
+                                  k.ptr(g_v, self.np_dtype), k.ptr(g_b, self.np_dtype),
+                                  k.ptr(g_phi, self.np_dtype), k.ptr(g_mu, self.np_dtype),
+                                  iters.ctypes.data, theta.ctypes.data)
+        self._check(st, allow_nc=True)
+        if self.n_scenes == 1:
+            return g_b, g_phi, g_mu, int(iters[0]), float(theta[0])
+        return g_b, g_phi, g_mu, iters, theta
 
     def get_w(self, out=None):
         out = self._out(self.n, out)
