@@ -173,7 +173,7 @@ def batched_bench(args, torch, dev, stream, rank):
     sc = scenes.lattice_batch(args.batch_scenes, seed=scenes.SEED_BASE + 4 + 1000 * rank)
     meta = sc.meta
     S = len(meta["sides"])
-    nq = meta["sides"].astype(np.int64) ** 3
+    nq = meta["nodes"].astype(np.int64)
     dof_scene = np.repeat(np.arange(S), 3 * nq)
     comp = np.tile(np.arange(3), int(nq.sum()))
     h = sc.h
@@ -231,9 +231,10 @@ def batched_bench(args, torch, dev, stream, rank):
             kms.append(s.last_kernel_ms())
     its = np.array(its)
     env_sps = S * args.batch_steps / t_total
+    nc_q = np.bincount(np.searchsorted(sc.scene_ptr, sc.node_i, side="right") - 1, minlength=S)
     bytes_scene = np.array([
-        algorithmic_bytes_per_sweep(type("Q", (), dict(n_nodes=int(n), n=3 * int(n), nnzb=int(bq), n_c=int(s_ ** 2)))())
-        for n, bq, s_ in zip(nq, np.diff(sc.row_ptr[sc.scene_ptr]), meta["sides"])])
+        algorithmic_bytes_per_sweep(type("Q", (), dict(n_nodes=int(n), n=3 * int(n), nnzb=int(bq), n_c=int(c)))())
+        for n, bq, c in zip(nq, np.diff(sc.row_ptr[sc.scene_ptr]), nc_q)])
     alg = float((its * bytes_scene[None, :]).sum(axis=1).mean())
     k_avg = float(np.mean(kms)) / 1e3
     # plain per-scene solves (one context per scene) on a sample, same tolerance
@@ -271,6 +272,42 @@ def batched_bench(args, torch, dev, stream, rank):
     }
 
 
+def adjoint_bench(args, torch, dev, stream):
+    """256 rest-linearised 16x16x8 lattices (6,144 DOF each), a 64-step rollout
+    differentiated by torch autograd through the adjoint kernel, checkpointed
+    every 8 steps: wall time of the backward pass (recompute + adjoint solves)
+    over the forward pass."""
+    from paper_2201_09212_gb300 import scenes, vfpi
+    from paper_2201_09212_gb300.autograd import LatticeHarness, rollout
+    sc = scenes.lattice_batch(args.adj_scenes, seed=scenes.SEED_BASE + 5, dims=(16, 16, 8))
+    s = vfpi.Solver.from_scene(sc, theta_th=THETA_TH, l_max=L_MAX, norm="rms", stream=stream)
+    H = LatticeHarness(sc, dev)
+    res = {}
+    with torch.cuda.stream(stream):
+        for rep in range(2):                       # first pass warms up
+            v0 = torch.from_numpy(sc.v0).to(dev).requires_grad_(True)
+            mu = torch.from_numpy(sc.mu).to(dev).requires_grad_(True)
+            steps = 8 if rep == 0 else args.adj_steps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, _ = rollout(s, H, H.x_rest.clone(), v0, mu, steps, checkpoint=8)
+            L = H.com_z(x).sum()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            L.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            res = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                   "grad_norm_v0": float(v0.grad.norm()), "grad_norm_mu": float(mu.grad.norm())}
+    s.close()
+    return {
+        "workload": f"{args.adj_scenes} lattices 16x16x8 ({6144 * args.adj_scenes} DOF), "
+                    f"{args.adj_steps}-step rollout, checkpoint every 8, d(COM z)/d(v0, mu)",
+        "adjoint_forward_ratio": res["backward_s"] / res["forward_s"],
+        **res,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,6 +321,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=30)
     ap.add_argument("--per-scene-sample", type=int, default=32)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--adj-scenes", type=int, default=256)
+    ap.add_argument("--adj-steps", type=int, default=64)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -385,6 +425,10 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             batched["env_steps_per_s"] = args.batch_scenes * ws * 1e3 / float(t.item())
 
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = adjoint_bench(args, torch, dev, stream)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -421,6 +465,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "batched": batched,
+        "adjoint": adjoint,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

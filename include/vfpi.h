@@ -108,8 +108,27 @@ typedef struct {
   const int32_t* scene_ptr;/* [n_scenes+1] node offsets of the scenes (batched)     */
   int32_t block_threads;   /* 0 = default; threads per CTA of the solve kernel       */
   int32_t force_path;      /* 0 = auto, 1 = grid-wide kernel, 2 = CTA-per-scene      */
-  int32_t reserved[6];
+  int32_t kernel_variant;  /* grid path: one of VFPI_VARIANT_* (threads per CTA,
+                              CTAs/SM register budget, prefetch); with 0 a nonzero
+                              block_threads selects that CTA size, unbudgeted     */
+  int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
+                              fit, capped at one warp per 32-row slice)              */
+  int32_t reserved[4];
 } vfpi_opts;
+
+/* Grid-path kernel variants (threads per CTA / minimum CTAs per SM the register
+ * budget is set for / next-chunk register prefetch).  Pick with the tuner in
+ * paper_2201_09212_gb300/tune.py or by hand. */
+enum {
+  VFPI_VARIANT_DEFAULT = 0,      /* 256 threads, 3 CTAs/SM (80 registers)    */
+  VFPI_VARIANT_256_4 = 1,
+  VFPI_VARIANT_512_2 = 2,
+  VFPI_VARIANT_128_8 = 3,
+  VFPI_VARIANT_256_2_PF = 4,
+  VFPI_VARIANT_128_4_PF = 5,
+  VFPI_VARIANT_512_1_PF = 6,
+  VFPI_VARIANT_256_2 = 7
+};
 
 /* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,
  * strict operator, absolute norm, one scene. */

@@ -79,7 +79,7 @@ class LatticeHarness:
         meta = scene.meta
         h = scene.h
         if meta.get("kind") == "lattice_batch":
-            nq = meta["sides"].astype(np.int64) ** 3
+            nq = meta["nodes"].astype(np.int64)
             dof_scene = np.repeat(np.arange(len(nq)), 3 * nq)
             g = meta["gravity"][dof_scene, np.tile(np.arange(3), int(nq.sum()))]
             kappa = (h * meta["k"] / meta["coef"])[dof_scene]
@@ -105,16 +105,17 @@ class LatticeHarness:
         return b, phi
 
     def com_z(self, x):
-        """Height of each scene's centre of mass, [n_scenes]."""
+        """Height of each scene's centre of mass, [n_scenes] (a fixed-order
+        reduction: prefix sums differenced at the scene boundaries)."""
         z = x[2::3]
         ptr = torch.as_tensor(self.scene_ptr, device=x.device, dtype=torch.int64)
-        counts = ptr[1:] - ptr[:-1]
-        idx = torch.repeat_interleave(torch.arange(len(counts), device=x.device), counts)
-        return torch.zeros(len(counts), dtype=x.dtype, device=x.device).index_add_(0, idx, z) / counts
+        c = torch.cat([torch.zeros(1, dtype=z.dtype, device=z.device), torch.cumsum(z, 0)])
+        return (c[ptr[1:]] - c[ptr[:-1]]) / (ptr[1:] - ptr[:-1]).to(z.dtype)
 
 
 def rollout(solver, harness, x0, v0, mu, steps, checkpoint=8):
-    """Positions after ``steps`` time steps, differentiable in ``v0`` and ``mu``."""
+    """Positions and velocities after ``steps`` time steps, differentiable in
+    ``v0`` and ``mu``; ``checkpoint`` <= 0 stores every step instead."""
 
     def segment(x, v, mu_, n):
         for _ in range(n):
@@ -126,8 +127,8 @@ def rollout(solver, harness, x0, v0, mu, steps, checkpoint=8):
     x, v = x0, v0
     k = 0
     while k < steps:
-        n = min(checkpoint, steps - k)
-        if checkpoint and torch.is_grad_enabled():
+        n = min(checkpoint, steps - k) if checkpoint > 0 else steps - k
+        if checkpoint > 0 and torch.is_grad_enabled():
             x, v = ckpt.checkpoint(segment, x, v, mu, n, use_reentrant=False)
         else:
             x, v = segment(x, v, mu, n)

@@ -601,6 +601,18 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
   if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   c->nt = o->block_threads ? o->block_threads : (c->path == 1 ? 256 : 128);
+  if (o->kernel_variant < 0 || o->kernel_variant > VFPI_VARIANT_256_2) {
+    c->err = "unknown kernel_variant";
+    return fail(VFPI_ERR_INVALID_ARG);
+  }
+  if (c->path == 1 && (o->kernel_variant > 0 || !o->block_threads)) {
+    static const int table[8][3] = {{256, 3, 0}, {256, 4, 0}, {512, 2, 0}, {128, 8, 0},
+                                    {256, 2, 1}, {128, 4, 1}, {512, 1, 1}, {256, 2, 0}};
+    c->nt = table[o->kernel_variant][0];
+    c->minb = table[o->kernel_variant][1];
+    c->pf = table[o->kernel_variant][2];
+  }
+  if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
   CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(cudaStreamSynchronize(st));

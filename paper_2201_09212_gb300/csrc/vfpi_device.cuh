@@ -200,6 +200,68 @@ __device__ __forceinline__ void row_product(const DevProblem<T>& P, int slice, i
   }
 }
 
+// Same product with the next chunk's columns and values loaded into registers
+// while the current chunk's gathers and FMAs run (twice the bytes in flight
+// per warp, same arithmetic in the same order).
+template <typename T>
+__device__ __forceinline__ void row_product_prefetch(const DevProblem<T>& P, int slice, int lane,
+                                                     const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  const int len = P.slice_len[slice];
+  const int64_t off = P.slice_off[slice];
+  const T* __restrict__ vb = P.vals + off * 288;
+  const int32_t* __restrict__ cb = P.cols + off * 32;
+  a0 = T(0); a1 = T(0); a2 = T(0);
+  const int nfull = len / VW;
+  int c[VW];
+  T m[9][VW];
+  if (nfull > 0) {
+    Chunk<T>::cols(cb + lane * VW, c);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Chunk<T>::vals(vb + lane * VW + q * (32 * VW), m[q]);
+  }
+#pragma unroll 1
+  for (int k = 0; k < nfull; ++k) {
+    int cn[VW];
+    T mn[9][VW];
+    const bool more = k + 1 < nfull;
+    if (more) {
+      Chunk<T>::cols(cb + (int64_t)(k + 1) * (32 * VW) + lane * VW, cn);
+      const T* p = vb + (int64_t)(k + 1) * (288 * VW) + lane * VW;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Chunk<T>::vals(p + q * (32 * VW), mn[q]);
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const Vec4<T> x = ldv(vin + c[e]);
+      a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
+      a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
+      a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
+    }
+    if (more) {
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        c[e] = cn[e];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) m[q][e] = mn[q][e];
+      }
+    }
+  }
+  const int ntail = len - nfull * VW;
+  const T* pt = vb + (int64_t)nfull * (288 * VW) + lane;
+  const int32_t* ct = cb + (int64_t)nfull * (32 * VW) + lane;
+  for (int t = 0; t < ntail; ++t) {
+    const int cc = __ldcs(ct + t * 32);
+    T mm[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) mm[q] = __ldcs(pt + t * 288 + q * 32);
+    const Vec4<T> x = ldv(vin + cc);
+    a0 = fma(mm[0], x.x, fma(mm[1], x.y, fma(mm[2], x.z, a0)));
+    a1 = fma(mm[3], x.x, fma(mm[4], x.y, fma(mm[5], x.z, a1)));
+    a2 = fma(mm[6], x.x, fma(mm[7], x.y, fma(mm[8], x.z, a2)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one-shot contact solve (Alg. 2, strict operator of eq. operator)
 // ---------------------------------------------------------------------------
@@ -297,11 +359,12 @@ __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
 // One row of one sweep: returns this row's contribution to ||dv||^2 (0 for a
 // D-contact node, whose update happens in phase 2).  ADJ selects the adjoint
 // sweep (b is then dL/dv and the contact step is the frozen linear map).
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool PF = false>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
                                             const Vec4<T>* vin, Vec4<T>* vout) {
   T a0, a1, a2;
-  row_product(P, slice, lane, vin, a0, a1, a2);
+  if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
+  else row_product(P, slice, lane, vin, a0, a1, a2);
   const int row = slice * 32 + lane;
   const Vec4<T> vo = ldv(vin + row);
   const Vec4<T> bb = ldv(P.b + row);
@@ -446,8 +509,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
 // gw, gw + W, ...; one barrier per sweep (two with D-contacts).  theta is the
 // fixed-order sum of the per-CTA partials, computed identically by every CTA,
 // so all CTAs take the same stop decision without a further exchange.
-template <typename T, int NT, bool ADJ>
-__global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
+template <typename T, int NT, int MINB, bool PF, bool ADJ>
+__global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[33];
   __shared__ int s_ok;
   const int lane = threadIdx.x & 31;
@@ -459,7 +522,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(DevProblem<T> P, SolveCtl ctl
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     double acc = 0.0;
-    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout);
+    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout);
     if (ctl.n_d > 0) {
       if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
       for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)

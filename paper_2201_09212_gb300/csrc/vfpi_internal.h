@@ -85,6 +85,8 @@ struct vfpi_ctx {
   int path = 0;    // 1 grid-wide cooperative kernel, 2 CTA per scene
   int grid = 0;    // CTAs
   int nt = 0;      // threads per CTA
+  int minb = 1;    // grid path: minimum CTAs per SM the kernel is compiled for
+  int pf = 0;      // grid path: register prefetch of the next chunk
   int max_grid = 0;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -152,24 +152,35 @@ cudaError_t Launch<T>::spmv(vfpi_ctx* c, const void* x_int, void* y_int) {
   return cudaGetLastError();
 }
 
-// Kernel selection by threads per CTA and mode.
-template <typename T, int NT>
-struct Kernels {
-  static void* get(int path, bool adj) {
-    if (path == 1) return adj ? (void*)&k_solve_grid<T, NT, true> : (void*)&k_solve_grid<T, NT, false>;
-    return adj ? (void*)&k_solve_scenes<T, NT, true> : (void*)&k_solve_scenes<T, NT, false>;
-  }
-};
+// Grid-path kernel variants: (threads per CTA, minimum CTAs per SM for the
+// register budget, register prefetch of the next chunk).
+template <typename T>
+static void* grid_kernel(int nt, int minb, int pf, bool adj) {
+#define VFPI_GK(NT_, MB_, PF_)                                                          \
+  if (nt == NT_ && minb == MB_ && pf == PF_)                                            \
+    return adj ? (void*)&k_solve_grid<T, NT_, MB_, PF_ != 0, true>                      \
+               : (void*)&k_solve_grid<T, NT_, MB_, PF_ != 0, false>;
+  VFPI_GK(64, 1, 0) VFPI_GK(128, 1, 0) VFPI_GK(256, 1, 0) VFPI_GK(512, 1, 0)
+  VFPI_GK(256, 3, 0) VFPI_GK(256, 4, 0) VFPI_GK(512, 2, 0) VFPI_GK(128, 8, 0)
+  VFPI_GK(256, 2, 1) VFPI_GK(128, 4, 1) VFPI_GK(512, 1, 1) VFPI_GK(256, 2, 0)
+#undef VFPI_GK
+  return nullptr;
+}
 
 template <typename T>
-static void* pick_kernel(int path, int nt, bool adj = false) {
+static void* scenes_kernel(int nt, bool adj) {
   switch (nt) {
-    case 64: return Kernels<T, 64>::get(path, adj);
-    case 128: return Kernels<T, 128>::get(path, adj);
-    case 256: return Kernels<T, 256>::get(path, adj);
-    case 512: return Kernels<T, 512>::get(path, adj);
+    case 64: return adj ? (void*)&k_solve_scenes<T, 64, true> : (void*)&k_solve_scenes<T, 64, false>;
+    case 128: return adj ? (void*)&k_solve_scenes<T, 128, true> : (void*)&k_solve_scenes<T, 128, false>;
+    case 256: return adj ? (void*)&k_solve_scenes<T, 256, true> : (void*)&k_solve_scenes<T, 256, false>;
+    case 512: return adj ? (void*)&k_solve_scenes<T, 512, true> : (void*)&k_solve_scenes<T, 512, false>;
     default: return nullptr;
   }
+}
+
+template <typename T>
+static void* pick_kernel(vfpi_ctx* c, bool adj) {
+  return c->path == 1 ? grid_kernel<T>(c->nt, c->minb, c->pf, adj) : scenes_kernel<T>(c->nt, adj);
 }
 
 template <typename T>
@@ -181,7 +192,7 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
     return e;
   int per_sm = 0;
   for (int adj = 0; adj < 2; ++adj) {  // one grid fits both modes
-    void* k = pick_kernel<T>(c->path, c->nt, adj != 0);
+    void* k = pick_kernel<T>(c, adj != 0);
     if (!k) return cudaErrorInvalidValue;
     int q = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, 0)) != cudaSuccess) return e;
@@ -194,6 +205,7 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
     // than there are warps' worth of slices
     const int need = (c->n_slices + c->nt / 32 - 1) / (c->nt / 32);
     c->grid = std::max(1, std::min(c->max_grid, need));
+    if (c->opts.grid_ctas > 0) c->grid = std::min(c->max_grid, c->opts.grid_ctas);
   } else {
     c->grid = std::max(1, std::min(c->max_grid, c->n_scenes));
   }
@@ -226,7 +238,7 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
   DevProblem<T> P = dev_problem<T>(c, adjoint);
   void* args[] = {&P, &ctl};
-  void* k = pick_kernel<T>(c->path, c->nt, adjoint);
+  void* k = pick_kernel<T>(c, adjoint);
   if (!k) return cudaErrorInvalidValue;
   // inside a stream capture the events become graph nodes that record on replay
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -484,7 +484,7 @@ def random_problem(rng, n_nodes, n_contacts, *, density=0.3, d_contacts=0,
 
 def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-3,
                   k_scale_range=(0.5, 2.0), mu_range=(0.2, 0.8), v_down=0.1, v_sigma=1e-3,
-                  spacing=0.01, dtype=np.float32) -> Scene:
+                  spacing=0.01, dtype=np.float32, dims=None) -> Scene:
     """``n_scenes`` independent rest-linearized cubic lattices on the ground plane,
     concatenated into one batched problem (vectorised; same physics as
     :func:`batched_lattices`).
@@ -494,23 +494,33 @@ def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-
     stiffness.  Per scene: side ``U{side_range}``, ``k = 1e3 * U[k_scale_range]``,
     gravity tilted by U[0, 30] degrees, friction ``mu ~ U[mu_range]`` per contact;
     bottom layer on ``z = 0`` (phi = 0).  ``meta`` carries per-scene arrays
-    (side, k, coef = h c + h^2 k, gravity) for dynamics harnesses.
+    (side, k, coef = h c + h^2 k, gravity) for dynamics harnesses.  ``dims``
+    fixes every scene to ``nx x ny x nz`` nodes instead of random cubes.
     """
     rng = np.random.default_rng(seed)
-    sides = rng.integers(side_range[0], side_range[1] + 1, size=n_scenes)
+    if dims is None:
+        sides = rng.integers(side_range[0], side_range[1] + 1, size=n_scenes)
+        shape = {int(s): (int(s),) * 3 for s in np.unique(sides)}
+    else:
+        sides = np.zeros(n_scenes, dtype=np.int64)      # one shape, key 0
+        shape = {0: tuple(int(d) for d in dims)}
     kk = 1e3 * rng.uniform(*k_scale_range, size=n_scenes)
     grav = np.array([tilted_gravity(rng) for _ in range(n_scenes)])
     coef = h * c + h * h * kk
     tmpl = {}
     for s in np.unique(sides):
         s = int(s)
-        ix, iy, iz = _grid_index(s, s, s)
+        nx, ny, nz = shape[s]
+        nn = nx * ny * nz
+        ix, iy, iz = _grid_index(nx, ny, nz)
         x = np.stack([ix, iy, iz], axis=1) * spacing
-        rp, col, L, _ = lattice_system(s, s, s, x, x, np.zeros((s ** 3, 3)), mass=0.0, k=1.0,
+        rp, col, L, _ = lattice_system(nx, ny, nz, x, x, np.zeros((nn, 3)), mass=0.0, k=1.0,
                                        c=0.0, h=1.0, gravity=(0, 0, 0), dtype=np.float64)
-        diag = np.nonzero(col == np.repeat(np.arange(s ** 3), np.diff(rp)))[0]
+        diag = np.nonzero(col == np.repeat(np.arange(nn), np.diff(rp)))[0]
         tmpl[s] = (rp, col, L.astype(np.float64), diag, x)
-    N_q = sides ** 3
+    nodes_of = {s: int(np.prod(shape[s])) for s in shape}
+    base_of = {s: shape[s][0] * shape[s][1] for s in shape}
+    N_q = np.array([nodes_of[int(s)] for s in sides], dtype=np.int64)
     node_off = np.zeros(n_scenes + 1, dtype=np.int64)
     node_off[1:] = np.cumsum(N_q)
     nnzb_q = np.array([tmpl[int(s)][1].shape[0] for s in sides])
@@ -526,11 +536,12 @@ def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-
         s = int(s)
         rp, cl, L, diag, xs = tmpl[s]
         qs = np.nonzero(sides == s)[0]
+        nn = nodes_of[s]
         for q in qs:
             n0, b0 = node_off[q], blk_off[q]
-            row_ptr[n0:n0 + s ** 3] = rp[:-1] + b0
+            row_ptr[n0:n0 + nn] = rp[:-1] + b0
             col[b0:b0 + cl.shape[0]] = cl + n0
-            x0[n0:n0 + s ** 3] = xs
+            x0[n0:n0 + nn] = xs
         # values of the whole group at once: coef_q * L + M on the diagonal blocks
         blk = coef[qs][:, None, None, None] * L[None]
         blk[:, diag] += mass * eye
@@ -544,7 +555,8 @@ def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-
     scene_of = np.repeat(np.arange(n_scenes), N_q)
     g_node = grav[scene_of]
     b = (mass * v + h * mass * g_node).ravel()
-    bottom = np.concatenate([node_off[q] + np.arange(int(sides[q]) ** 2) for q in range(n_scenes)])
+    bottom = np.concatenate([node_off[q] + np.arange(base_of[int(sides[q])])
+                             for q in range(n_scenes)])
     n_c = bottom.shape[0]
     R = contact_frames(np.tile([0.0, 0.0, 1.0], (n_c, 1)))
     return Scene(
@@ -554,5 +566,5 @@ def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-
         mu=rng.uniform(*mu_range, size=n_c).astype(dtype), phi=np.zeros(n_c, dtype=dtype),
         v0=v.ravel().astype(dtype), h=h, x0=x0.ravel(), mass=np.full(3 * N, mass),
         scene_ptr=node_off.astype(np.int32),
-        meta=dict(kind="lattice_batch", sides=sides, k=kk, coef=coef, gravity=grav,
-                  node_mass=mass, seed=seed))
+        meta=dict(kind="lattice_batch", sides=sides, nodes=N_q, k=kk, coef=coef, gravity=grav,
+                  node_mass=mass, seed=seed, dims=dims))

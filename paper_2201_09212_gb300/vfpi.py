@@ -55,7 +55,8 @@ class _Opts(C.Structure):
                 ("w_user", C.c_void_p), ("theta_th", C.c_double), ("l_max", C.c_int32),
                 ("operator_", C.c_int32), ("residual_norm", C.c_int32), ("n_scenes", C.c_int32),
                 ("scene_ptr", C.c_void_p), ("block_threads", C.c_int32),
-                ("force_path", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("force_path", C.c_int32), ("kernel_variant", C.c_int32),
+                ("grid_ctas", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 _LIB = None
@@ -159,7 +160,7 @@ class Solver:
     def __init__(self, row_ptr, col_idx, vals, b, node_i, node_j, R, mu, phi, *, h=1e-3,
                  dtype="f32", w_mode="frobenius", alpha=0.0, w_user=None, theta_th=1e-5,
                  l_max=200, norm="abs", scene_ptr=None, block_threads=0, force_path=0,
-                 stream=None):
+                 kernel_variant=0, grid_ctas=0, stream=None):
         self._L = lib()
         self.dtype_code, self.np_dtype = DTYPES[dtype]
         self.n_nodes = int(len(row_ptr) - 1)
@@ -186,6 +187,8 @@ class Solver:
         o.scene_ptr = k.ptr(scene_ptr, np.int32)
         o.block_threads = int(block_threads)
         o.force_path = int(force_path)
+        o.kernel_variant = int(kernel_variant)
+        o.grid_ctas = int(grid_ctas)
         self.h = float(h)
         self.stream = stream
         sptr = None
