@@ -207,14 +207,24 @@ vfpi_status vfpi_integrate(vfpi_t ctx, double* x_inout);
  * the method (Sec. III.F), exposed for residual checks and dynamics harnesses. */
 vfpi_status vfpi_matvec(vfpi_t ctx, const void* x, void* y);
 
+/* Change the launch shape of the solve kernels after create (the tuner's
+ * knob): kernel_variant and grid_ctas as in vfpi_opts (grid path),
+ * block_threads for either path.  Synchronises. */
+vfpi_status vfpi_configure_launch(vfpi_t ctx, int32_t kernel_variant, int32_t block_threads,
+                                  int32_t grid_ctas);
+
 /* Device time in milliseconds of the most recent solve kernel, measured with
  * CUDA events recorded on the context's stream around that launch. */
 vfpi_status vfpi_last_kernel_ms(vfpi_t ctx, float* ms);
 
 /* Sizes of the device layout: [0] padded nodes, [1] slices of 32 rows,
  * [2] stored block slots (incl. padding), [3] kernel path (1 grid, 2 CTA per
- * scene), [4] CTAs of the solve launch, [5] threads per CTA. */
-vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info6);
+ * scene), [4] CTAs of the solve launch, [5] threads per CTA, [6] CTAs that can
+ * be resident at once, [7] SMs of the device. */
+vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info8);
+
+/* Replace theta_th and l_max of Alg. 1 for later solves (and the adjoint). */
+vfpi_status vfpi_set_tolerance(vfpi_t ctx, double theta_th, int32_t l_max);
 
 /* ------------------------------------------------------------------------
  * Allocation-free solve.  The paper has no counterpart to this entry point.

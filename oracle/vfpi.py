@@ -227,3 +227,52 @@ def solve(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, l_max: int
 def integrate(x: np.ndarray, v: np.ndarray, h: float) -> np.ndarray:
     """State update ``x_{k+1} = x_k + h v_hat`` (eq. disc_dyn, backward-Euler reading)."""
     return np.asarray(x, dtype=np.float64) + h * np.asarray(v, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Chebyshev acceleration (Alg. 3)
+# ----------------------------------------------------------------------------
+
+def chebyshev_nu(l: int, l_s: int, rho: float, nu_prev: float) -> float:
+    """The weight nu_{l+1} of Alg. 3: 1 before the slow start ``l_s``,
+    ``2 / (2 - rho^2)`` at ``l = l_s`` and ``4 / (4 - rho^2 nu_l)`` after."""
+    if l < l_s:
+        return 1.0
+    if l == l_s:
+        return 2.0 / (2.0 - rho * rho)
+    return 4.0 / (4.0 - rho * rho * nu_prev)
+
+
+def solve_chebyshev(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, l_max: int,
+                    l_s: int = 10, u: float = 0.9, operator: str = STRICT,
+                    norm: str = NORM_ABS, rho_fixed: float | None = None) -> SolveResult:
+    """Alg. 3: the V-FPI step gives ``v**`` (eq. pgd1, Alg. 2, eq. vup); then
+    ``v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}`` (eq. chebyup with
+    the under-relaxation ``u`` of the text; ``u = 1`` is the printed update),
+    ``theta = ||v^{l+1} - v^l||``, and after the stop test
+    ``rho = min(||v^l - v^{l-1}|| / ||v^{l-1} - v^{l-2}||, 1)`` (eq. varrho, taken
+    with the current l).  Needs ``l_s >= 3`` so that rho exists when first used;
+    ``rho_fixed`` replaces the estimate by a given spectral radius (then
+    ``l_s >= 2``)."""
+    if l_s < (2 if rho_fixed is not None else 3):
+        raise ValueError("l_s too small")
+    v = np.asarray(v0, dtype=np.float64).copy()
+    v_prev = v.copy()
+    thetas, nu, rho = [], 1.0, (0.0 if rho_fixed is None else float(rho_fixed))
+    l = 1
+    while True:
+        r = sweep(P, w, v, operator, norm)
+        nu = chebyshev_nu(l, l_s, rho, nu)
+        v_next = nu * (u * (r.v_next - v) + v - v_prev) + v_prev
+        dv = v_next - v
+        theta = math.sqrt(math.fsum(dv * dv))
+        if norm == NORM_RMS:
+            theta /= math.sqrt(P.n)
+        thetas.append(theta)
+        if theta < theta_th or l == l_max:
+            break
+        if l >= 3 and rho_fixed is None:
+            rho = min(thetas[l - 2] / thetas[l - 3], 1.0) if thetas[l - 3] > 0 else 1.0
+        v_prev, v = v, v_next
+        l += 1
+    return SolveResult(v_next, r.lam, r.lam_star, l, theta, theta < theta_th, thetas)

@@ -598,6 +598,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
 
   // kernel path and launch shape
   c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
+  c->opts.grid_ctas = o->grid_ctas;
   if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
   if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   c->nt = o->block_threads ? o->block_threads : (c->path == 1 ? 256 : 128);
@@ -867,6 +868,43 @@ vfpi_status vfpi_matvec(vfpi_t c, const void* x, void* y) {
   return export_vec(c, c->d_t1, y);
 }
 
+vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t block_threads,
+                                  int32_t grid_ctas) {
+  CTX_CHECK(c);
+  if (kernel_variant < 0 || kernel_variant > VFPI_VARIANT_256_2)
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "unknown kernel_variant");
+  if (block_threads && block_threads != 64 && block_threads != 128 && block_threads != 256 &&
+      block_threads != 512)
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
+  if (grid_ctas < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "grid_ctas must be >= 0");
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  const int nt0 = c->nt, mb0 = c->minb, pf0 = c->pf, g0 = c->opts.grid_ctas;
+  c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
+  c->minb = 1;
+  c->pf = 0;
+  if (c->path == 1 && (kernel_variant > 0 || !block_threads)) {
+    static const int table[8][3] = {{256, 3, 0}, {256, 4, 0}, {512, 2, 0}, {128, 8, 0},
+                                    {256, 2, 1}, {128, 4, 1}, {512, 1, 1}, {256, 2, 0}};
+    c->nt = table[kernel_variant][0];
+    c->minb = table[kernel_variant][1];
+    c->pf = table[kernel_variant][2];
+  }
+  c->opts.grid_ctas = grid_ctas;
+  const int old_max = c->max_grid;
+  cudaError_t e = DISPATCH(c, configure(c));
+  if (e != cudaSuccess) {
+    c->nt = nt0; c->minb = mb0; c->pf = pf0; c->opts.grid_ctas = g0;
+    DISPATCH(c, configure(c));
+    return cuda_fail(c, e, "configure");
+  }
+  if (c->max_grid > old_max) {
+    if (c->d_partials) cudaFree(c->d_partials);
+    c->d_partials = nullptr;
+    VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)c->max_grid));
+  }
+  return VFPI_OK;
+}
+
 vfpi_status vfpi_last_kernel_ms(vfpi_t c, float* ms) {
   CTX_CHECK(c);
   if (!ms) return arg_fail(c, VFPI_ERR_INVALID_ARG, "ms is NULL");
@@ -879,12 +917,26 @@ vfpi_status vfpi_last_kernel_ms(vfpi_t c, float* ms) {
 vfpi_status vfpi_get_layout(vfpi_t c, int64_t* info) {
   CTX_CHECK(c);
   if (!info) return arg_fail(c, VFPI_ERR_INVALID_ARG, "info is NULL");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
   info[0] = c->n_pad;
   info[1] = c->n_slices;
   info[2] = 32 * c->n_entries;
   info[3] = c->path;
   info[4] = c->grid;
   info[5] = c->nt;
+  info[6] = c->max_grid;
+  info[7] = sms;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_tolerance(vfpi_t c, double theta_th, int32_t l_max) {
+  CTX_CHECK(c);
+  if (l_max < 1) return arg_fail(c, VFPI_ERR_INVALID_ARG, "l_max must be >= 1");
+  c->opts.theta_th = theta_th;
+  c->opts.l_max = l_max;
   return VFPI_OK;
 }
 

@@ -1,0 +1,96 @@
+"""Launch-shape autotuner for the V-FPI solve kernels.
+
+For a solver already built on its problem, ``tune`` times candidate launch
+shapes -- for the grid-wide kernel: the kernel variant (threads per CTA, the
+CTAs-per-SM register budget, next-chunk prefetch) and the number of persistent
+CTAs (all that fit, the fewest that keep the same slices per warp, whole
+multiples of the SM count); for the CTA-per-scene kernel: the threads per CTA
+(warps working on one scene) -- each over a fixed number of sweeps of the
+solver's own problem, timed with CUDA events, and keeps the fastest.  Results
+are cached in a JSON file keyed by the layout signature and the GPU name, so a
+later solver of the same shape reuses them without timing.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
+GRID_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7)
+WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8}
+
+
+def _signature(solver, gpu: str) -> str:
+    lay = solver.layout()
+    return f"{gpu}|path{lay['path']}|slices{lay['n_slices']}|slots{lay['slots']}|" \
+           f"scenes{solver.n_scenes}|{solver.np_dtype.__name__}"
+
+
+def _grid_candidates(n_slices, warps, max_grid, sms):
+    need = math.ceil(n_slices / warps)
+    out = {0}
+    k = math.ceil(n_slices / (max_grid * warps))
+    out.add(min(max_grid, math.ceil(n_slices / (warps * k))))
+    for r in range(1, max_grid // sms + 1):
+        out.add(min(need, r * sms))
+    return sorted(g for g in out if g == 0 or g <= max_grid)
+
+
+def _time(solver, sweeps, reps):
+    best = float("inf")
+    for _ in range(reps):
+        solver.solve_async()
+        solver.status()
+        best = min(best, solver.last_kernel_ms())
+    return best
+
+
+def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CACHE,
+         force: bool = False) -> dict:
+    """Pick and apply the fastest launch shape; returns it with its timings."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = _signature(solver, gpu)
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if key in table and not force:
+        best = table[key]
+        solver.configure_launch(best["kernel_variant"], best["block_threads"], best["grid_ctas"])
+        return dict(best, cached=True)
+    lay = solver.layout()
+    theta0, lmax0 = solver._theta_th, solver._l_max
+    solver.set_tolerance(-1.0, sweeps)
+    trials = []
+    if lay["path"] == 1:
+        for var in GRID_VARIANTS:
+            solver.configure_launch(var, 0, 0)
+            l2 = solver.layout()
+            for g in _grid_candidates(l2["n_slices"], WARPS[var], l2["max_grid"], l2["sms"]):
+                solver.configure_launch(var, 0, g)
+                ms = _time(solver, sweeps, reps)
+                trials.append(dict(kernel_variant=var, block_threads=0, grid_ctas=g,
+                                   ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
+    else:
+        for bt in (64, 128, 256):
+            solver.configure_launch(0, bt, 0)
+            ms = _time(solver, sweeps, reps)
+            trials.append(dict(kernel_variant=0, block_threads=bt, grid_ctas=0,
+                               ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
+    solver.set_tolerance(theta0, lmax0)
+    best = min(trials, key=lambda t: t["ms_per_sweep"])
+    solver.configure_launch(best["kernel_variant"], best["block_threads"], best["grid_ctas"])
+    result = dict(best, trials=trials)
+    if cache:
+        table[key] = {k: best[k] for k in ("kernel_variant", "block_threads", "grid_ctas",
+                                           "ms_per_sweep", "grid")}
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return dict(result, cached=False)

@@ -30,6 +30,7 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
+            "vfpi_configure_launch", "vfpi_set_tolerance",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
             "vfpi_noalloc_last_error")
 
@@ -95,6 +96,8 @@ def lib():
         "vfpi_integrate": (st, [vp, vp]),
         "vfpi_matvec": (st, [vp, vp, vp]),
         "vfpi_last_kernel_ms": (st, [vp, vp]),
+        "vfpi_configure_launch": (st, [vp, i32, i32, i32]),
+        "vfpi_set_tolerance": (st, [vp, C.c_double, i32]),
         "vfpi_get_layout": (st, [vp, vp]),
         "vfpi_last_error": (C.c_char_p, [vp]),
         "vfpi_status_string": (C.c_char_p, [st]),
@@ -190,6 +193,7 @@ class Solver:
         o.kernel_variant = int(kernel_variant)
         o.grid_ctas = int(grid_ctas)
         self.h = float(h)
+        self._theta_th, self._l_max = float(theta_th), int(l_max)
         self.stream = stream
         sptr = None
         if stream is not None:
@@ -361,13 +365,21 @@ class Solver:
         self._check(self._L.vfpi_matvec(self._h, k.ptr(x, self.np_dtype), k.ptr(out, self.np_dtype)))
         return out
 
+    def configure_launch(self, kernel_variant=0, block_threads=0, grid_ctas=0):
+        self._check(self._L.vfpi_configure_launch(self._h, int(kernel_variant), int(block_threads),
+                                                  int(grid_ctas)))
+
     def last_kernel_ms(self) -> float:
         ms = C.c_float()
         self._check(self._L.vfpi_last_kernel_ms(self._h, C.byref(ms)))
         return float(ms.value)
 
+    def set_tolerance(self, theta_th, l_max):
+        self._check(self._L.vfpi_set_tolerance(self._h, float(theta_th), int(l_max)))
+        self._theta_th, self._l_max = float(theta_th), int(l_max)
+
     def layout(self) -> dict:
-        info = (C.c_int64 * 6)()
+        info = (C.c_int64 * 8)()
         self._check(self._L.vfpi_get_layout(self._h, info))
-        keys = ("n_pad", "n_slices", "slots", "path", "grid", "threads")
+        keys = ("n_pad", "n_slices", "slots", "path", "grid", "threads", "max_grid", "sms")
         return dict(zip(keys, (int(x) for x in info)))

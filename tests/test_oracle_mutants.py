@@ -15,6 +15,7 @@ import pytest
 
 import oracle.vfpi as ov
 import oracle.adjoint as oadj
+from tests import test_oracle_chebyshev as cheb
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -39,6 +40,11 @@ MUTANTS = {
     "adjoint_no_transpose": (oadj, "adjoint", "np.linalg.solve((np.eye(n) - D).T,",
                              "np.linalg.solve((np.eye(n) - D),"),
     "adjoint_mu_sign": (oadj, "strict_jacobian", "dmu[1:] = ln * t", "dmu[1:] = -ln * t"),
+    "cheby_nu_first": (ov, "chebyshev_nu", "return 2.0 / (2.0 - rho * rho)", "return 2.0 / (2.0 - rho)"),
+    "cheby_nu_rec": (ov, "chebyshev_nu", "return 4.0 / (4.0 - rho * rho * nu_prev)",
+                     "return 4.0 / (4.0 - rho * nu_prev)"),
+    "cheby_anchor": (ov, "solve_chebyshev", "v_next = nu * (u * (r.v_next - v) + v - v_prev) + v_prev",
+                     "v_next = nu * (u * (r.v_next - v) + v - v_prev) + v"),
 }
 
 
@@ -62,13 +68,16 @@ def _pin_suite():
         lambda: pins.test_fixed_point_is_in_enumerated_scc_set(2, 17),
         lambda: pins.test_fixed_point_is_in_enumerated_scc_set(3, 21),
         lambda: pins.test_dense_adjoint_matches_central_differences(0),
+        lambda: cheb.test_nu_schedule_is_the_chebyshev_polynomial_ratio(),
+        lambda: cheb.test_same_fixed_point_and_fewer_iterations(0.9),
+        lambda: cheb.test_fixed_rho_is_the_textbook_chebyshev_semi_iteration(),
     ]
     for call in calls:
         try:
             with np.errstate(all="ignore"):
                 call()
-        except (AssertionError, np.linalg.LinAlgError, ValueError, FloatingPointError,
-                ZeroDivisionError, IndexError):
+        except (AssertionError, np.linalg.LinAlgError, ValueError, ArithmeticError,
+                IndexError):
             return False
     return True
 
