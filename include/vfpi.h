@@ -64,7 +64,10 @@ typedef enum {
 enum { VFPI_F32 = 0, VFPI_F64 = 1 };
 /* Choice of W (Sec. IV.C): Frobenius-norm minimiser, alpha * I, or caller's. */
 enum { VFPI_W_FROBENIUS = 0, VFPI_W_SCALAR = 1, VFPI_W_USER = 2 };
-/* ProjectFC (eq. operator).  Only the strict operator is built. */
+/* ProjectFC (eq. operator): strict (normal clamp, then the disk at mu lambda_n;
+ * exact SCC, used for all the paper's results but one) or proximal (Euclidean
+ * projection onto the cone; the fixed point is the convex contact problem of
+ * eq. ccp, Prop. 5, Thm. 2). */
 enum { VFPI_OP_STRICT = 0, VFPI_OP_PROXIMAL = 1 };
 /* Residual of Alg. 1: ||dv||_2 (paper) or ||dv||_2 / sqrt(n). */
 enum { VFPI_NORM_ABS = 0, VFPI_NORM_RMS = 1 };
@@ -113,7 +116,11 @@ typedef struct {
                               block_threads selects that CTA size, unbudgeted     */
   int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
                               fit, capped at one warp per 32-row slice)              */
-  int32_t reserved[4];
+  int32_t chebyshev_ls;    /* Chebyshev acceleration (Alg. 3): slow-start index
+                              l_s >= 3, or 0 for the plain iteration of Alg. 1     */
+  double chebyshev_u;      /* Alg. 3 under-relaxation u in (0, 1] (1 = the printed
+                              update of eq. chebyup)                               */
+  int32_t reserved[2];
 } vfpi_opts;
 
 /* Grid-path kernel variants (threads per CTA / minimum CTAs per SM the register
@@ -225,6 +232,21 @@ vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info8);
 
 /* Replace theta_th and l_max of Alg. 1 for later solves (and the adjoint). */
 vfpi_status vfpi_set_tolerance(vfpi_t ctx, double theta_th, int32_t l_max);
+
+/* Invertible contact model (eq. invt): Gamma_c + Omega_c in place of Gamma_c with
+ * Omega_m = omega_m I, omega [n_c] >= 0 in contact order (NULL: all zero).  The
+ * fixed point then satisfies the contact conditions for J v + phi e_n +
+ * omega lambda, and lambda = ProjectFC(-(J v + phi e_n) / omega) follows from
+ * the velocity alone.  Synchronises. */
+vfpi_status vfpi_set_regularization(vfpi_t ctx, const void* omega);
+
+/* Chebyshev acceleration of later solves (Alg. 3, eq. chebyup, eq. varrho):
+ * nu = 1 before the slow start l_s, 2 / (2 - rho^2) at l_s, then
+ * 4 / (4 - rho^2 nu); v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}
+ * with v** the V-FPI step and rho = min(||v^l - v^{l-1}|| / ||v^{l-1} - v^{l-2}||, 1).
+ * l_s = 0 switches it off; else l_s >= 3 and 0 < u <= 1.  The fixed point,
+ * W and the adjoint are unchanged. */
+vfpi_status vfpi_set_chebyshev(vfpi_t ctx, int32_t l_s, double u);
 
 /* ------------------------------------------------------------------------
  * Allocation-free solve.  The paper has no counterpart to this entry point.

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .vfpi import STRICT, gamma_blocks, sweep
+from .vfpi import PROXIMAL, STRICT, gamma_blocks, sweep
 
 
 def strict_jacobian(lam_star: np.ndarray, mu: float):
@@ -48,16 +48,51 @@ def strict_jacobian(lam_star: np.ndarray, mu: float):
     return Pp, dmu
 
 
-def adjoint(P, w: np.ndarray, v: np.ndarray, g_v: np.ndarray):
-    """Dense adjoint at the converged ``v``; returns ``(g_b, g_phi, g_mu, g_bar)``."""
-    r = sweep(P, w, v, STRICT)
+def proximal_jacobian(lam_star: np.ndarray, mu: float):
+    """``(P', dP/dmu)`` of the proximal operator (Euclidean projection onto the
+    friction cone, eq. operator) at one ``lambda*``.  Inside the cone: identity;
+    in its polar cone: zero; otherwise, with ``r = ||lambda*_t||``, ``t = lambda*_t / r``
+    and ``lambda_n = (lambda*_n + mu r) / (1 + mu^2)``:
+    ``dlambda_n = (d lambda*_n + mu t . d lambda*_t) / (1 + mu^2)``,
+    ``dlambda_t = mu t dlambda_n + mu (lambda_n / r)(I - t t^T) d lambda*_t``."""
+    a = float(lam_star[0])
+    r = float(np.hypot(lam_star[1], lam_star[2]))
+    Pp = np.zeros((3, 3))
+    dmu = np.zeros(3)
+    if r <= mu * a:
+        return np.eye(3), dmu
+    if mu * r <= -a:
+        return Pp, dmu
+    t = np.asarray(lam_star[1:], dtype=np.float64) / r
+    k = 1.0 + mu * mu
+    ln = (a + mu * r) / k
+    dln = np.concatenate([[1.0], mu * t]) / k                     # d lambda_n / d lambda*
+    Pp[0] = dln
+    Pp[1:] = mu * np.outer(t, dln)
+    Pp[1:, 1:] += mu * (ln / r) * (np.eye(2) - np.outer(t, t))
+    dln_dmu = (r * k - 2.0 * mu * (a + mu * r)) / (k * k)
+    dmu[0] = dln_dmu
+    dmu[1:] = (ln + mu * dln_dmu) * t
+    return Pp, dmu
+
+
+def adjoint(P, w: np.ndarray, v: np.ndarray, g_v: np.ndarray, operator: str = STRICT,
+            omega: np.ndarray | None = None):
+    """Dense adjoint at the converged ``v``; returns ``(g_b, g_phi, g_mu, g_bar)``.
+    ``omega`` ([n_c] scalars, the regularisation ``Omega_m = omega_m I`` of
+    eq. invt) enters through ``Gamma_m + Omega_m``."""
+    om = None if omega is None else np.asarray(omega, float)[:, None, None] * np.eye(3)
+    r = sweep(P, w, v, operator, omega=om)
     n = P.n
     Gam = gamma_blocks(P, w)
+    if om is not None:
+        Gam = Gam + om
     n_c = P.n_c
     B = np.zeros((3 * n_c, 3 * n_c))
     dmu = np.zeros((n_c, 3))
+    jac = strict_jacobian if operator == STRICT else proximal_jacobian
     for m in range(n_c):
-        Pp, dm = strict_jacobian(r.lam_star[m], P.mu[m])
+        Pp, dm = jac(r.lam_star[m], P.mu[m])
         B[3 * m:3 * m + 3, 3 * m:3 * m + 3] = Pp @ np.linalg.inv(Gam[m])
         dmu[m] = dm
     J = P.Jc.toarray()

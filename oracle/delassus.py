@@ -15,7 +15,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
-from .vfpi import project_strict
+from .vfpi import project_proximal, project_strict
 
 
 def delassus(P):
@@ -53,3 +53,33 @@ def pgs(P, tol: float = 1e-14, max_sweeps: int = 200000, relax: float = 1.0):
             break
     v = sla.cho_solve(chol, P.b + P.Jc.T @ lam)
     return v, lam.reshape(-1, 3), sweeps
+
+
+def ccp_apgd(P, omega=None, iters: int = 200000, tol: float = 1e-15):
+    """The convex contact problem (eq. ccp, with eq. invt's regularisation):
+    ``min 1/2 lambda^T (G + Omega) lambda + lambda^T (c + phi e_n)`` over the
+    product of friction cones, by accelerated projected gradient (Nesterov /
+    FISTA with the Euclidean cone projection and step 1 / L, L the largest
+    eigenvalue of G + Omega).  Returns ``(v, lambda [n_c, 3], iterations)``."""
+    G, c, chol = delassus(P)
+    n_c = P.n_c
+    H = G.copy()
+    if omega is not None:
+        H += np.kron(np.diag(np.asarray(omega, float)), np.eye(3))
+    q = c.copy()
+    q[0::3] += P.phi
+    L = np.linalg.eigvalsh(H).max()
+    lam = np.zeros(3 * n_c)
+    y = lam.copy()
+    tk = 1.0
+    it = 0
+    for it in range(1, iters + 1):
+        new = project_proximal(y - (H @ y + q) / L, P.mu).ravel()
+        tk1 = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * tk * tk))
+        y = new + ((tk - 1.0) / tk1) * (new - lam)
+        done = np.abs(new - lam).max() <= tol * max(np.abs(new).max(), 1e-300)
+        lam, tk = new, tk1
+        if done:
+            break
+    v = sla.cho_solve(chol, P.b + P.Jc.T @ lam)
+    return v, lam.reshape(-1, 3), it

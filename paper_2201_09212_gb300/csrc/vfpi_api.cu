@@ -120,8 +120,8 @@ cudaError_t out_view(vfpi_ctx* c, void* dst, size_t bytes, size_t slot, void** o
 void free_all(vfpi_ctx* c) {
   void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_vals, c->d_cols, c->d_b, c->d_w,
                   c->d_v0, c->d_v1, c->d_t0, c->d_t1, c->d_cslot, c->d_node_map, c->d_row_ptr, c->d_ds,
-                  c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi,
-                  c->d_lam, c->d_lam_star, c->d_scene_slice, c->d_scene_d, c->d_order,
+                  c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi, c->d_comega,
+                  c->d_lam, c->d_lam_star, c->d_dstar, c->d_scene_slice, c->d_scene_d, c->d_order,
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_stage};
@@ -241,7 +241,7 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   c->n_d = (int)dlist.size();
   int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist};
   for (auto p : ip) if (p) cudaFree(p);
-  void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_lam, c->d_lam_star};
+  void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_lam, c->d_lam_star, c->d_dstar};
   for (auto p : vp) if (p) cudaFree(p);
   VFPI_TRY_CUDA(dalloc(&c->d_ci, 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cj, 4 * (size_t)n_c));
@@ -250,8 +250,10 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(dalloc(&c->d_cR, c->esz * 9 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cmu, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cphi, c->esz * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_comega, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam, c->esz * 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam_star, c->esz * 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_dstar, c->esz * 8 * (size_t)n_c));
   cudaStream_t st = c->stream;
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_ci, c->h_ci.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cj, c->h_cj.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
@@ -260,6 +262,7 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cR, Rint.data(), Rint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cphi, phint.data(), phint.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_comega, 0, c->esz * (size_t)n_c, st));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_lam, 0, c->esz * 4 * (size_t)n_c, st));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_lam_star, 0, c->esz * 4 * (size_t)n_c, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cslot, cslot.data(), 4 * (size_t)c->n_pad, cudaMemcpyHostToDevice, st));
@@ -359,6 +362,8 @@ void vfpi_default_opts(vfpi_opts* o) {
   o->operator_ = VFPI_OP_STRICT;
   o->residual_norm = VFPI_NORM_ABS;
   o->n_scenes = 1;
+  o->chebyshev_ls = 0;
+  o->chebyshev_u = 1.0;
 }
 
 const char* vfpi_status_string(vfpi_status s) {
@@ -394,8 +399,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (!A || !b || !o) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "A, b and opts are required");
   if (o->dtype != VFPI_F32 && o->dtype != VFPI_F64)
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "dtype must be VFPI_F32 or VFPI_F64");
-  if (o->operator_ != VFPI_OP_STRICT)
-    return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "only the strict operator is built");
+  if (o->operator_ != VFPI_OP_STRICT && o->operator_ != VFPI_OP_PROXIMAL)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "operator_ must be VFPI_OP_STRICT or VFPI_OP_PROXIMAL");
   if (o->l_max < 1) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "l_max must be >= 1");
   if (o->w_mode < VFPI_W_FROBENIUS || o->w_mode > VFPI_W_USER)
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "unknown w_mode");
@@ -409,6 +414,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (o->block_threads && o->block_threads != 64 && o->block_threads != 128 &&
       o->block_threads != 256 && o->block_threads != 512)
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
+  if (o->chebyshev_ls != 0 && (o->chebyshev_ls < 3 || !(o->chebyshev_u > 0 && o->chebyshev_u <= 1)))
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
 
   vfpi_ctx* c = new (std::nothrow) vfpi_ctx;
   if (!c) return arg_fail(nullptr, VFPI_ERR_OOM, "host allocation failed");
@@ -929,6 +936,38 @@ vfpi_status vfpi_get_layout(vfpi_t c, int64_t* info) {
   info[5] = c->nt;
   info[6] = c->max_grid;
   info[7] = sms;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_regularization(vfpi_t c, const void* omega) {
+  CTX_CHECK(c);
+  if (c->n_c == 0) return VFPI_OK;
+  if (!omega) {
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_comega, 0, c->esz * (size_t)c->n_c, c->stream));
+    return VFPI_OK;
+  }
+  // host check: omega >= 0 and finite (n_c values)
+  std::vector<unsigned char> raw(c->esz * (size_t)c->n_c);
+  VFPI_TRY_CUDA(to_host(raw.data(), omega, raw.size(), c->stream));
+  for (int m = 0; m < c->n_c; ++m) {
+    const double x = c->dtype == VFPI_F64 ? reinterpret_cast<const double*>(raw.data())[m]
+                                          : (double)reinterpret_cast<const float*>(raw.data())[m];
+    if (!(x >= 0) || !std::isfinite(x))
+      return arg_fail(c, VFPI_ERR_INVALID_ARG, "omega must be finite and >= 0");
+  }
+  const void* d;
+  VFPI_TRY_CUDA(device_view(c, omega, raw.size(), 0, &d));
+  VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, d, c->d_comega, false)));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
+  CTX_CHECK(c);
+  if (l_s != 0 && (l_s < 3 || !(u > 0 && u <= 1)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  c->opts.chebyshev_ls = l_s;
+  c->opts.chebyshev_u = u;
   return VFPI_OK;
 }
 

@@ -59,12 +59,15 @@ struct DevProblem {
   const T* c_R;                  // [9][n_c] plane-major rotation entries
   const T* c_mu;                 // [n_c]
   const T* c_phi;                // [n_c]
+  const T* c_omega;              // [n_c] regularisation Omega_m = omega_m I (eq. invt)
+  int prox;                      // ProjectFC: 0 strict, 1 proximal (eq. operator)
   Vec4<T>* lam;                  // [n_c] lambda of the last sweep (n, t1, t2)
   Vec4<T>* lam_star;             // [n_c] lambda* of the last sweep
   const Vec4<T>* adj_ls;         // adjoint: frozen lambda* defining the active set
   T* adj_gphi;                   // adjoint: dL/dphi [n_c] (internal order)
   T* adj_gmu;                    // adjoint: dL/dmu  [n_c]
   const int32_t* d_list;         // D-contacts (internal contact ids)
+  Vec4<T>* dstar;                // [2 n_c] v* of the two nodes of a D-contact
   Vec4<T>* v0;                   // ping-pong iterates
   Vec4<T>* v1;
 };
@@ -85,7 +88,45 @@ struct SolveCtl {
   double* theta;                 // [n_scenes]
   int32_t n_d;                   // total D-contacts (grid path)
   int* err;                      // bit 0: a barrier wait ran out
+  int32_t cheb_ls;               // Alg. 3 slow start l_s (0: plain Alg. 1)
+  double cheb_u;                 // under-relaxation u
 };
+
+// Chebyshev acceleration (Alg. 3): weight of the current sweep and the
+// combination v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}.
+template <typename T>
+struct ChebStep {
+  int on;       // Alg. 3 active
+  int accel;    // l >= l_s: nu from the Chebyshev recurrence (else nu = 1)
+  T nu, u;
+};
+
+// nu_{l+1} of Alg. 3 from the slow-start index, the estimate rho and nu_l.
+__device__ __forceinline__ double cheb_nu(int l, int l_s, double rho, double nu_prev) {
+  if (l < l_s) return 1.0;
+  if (l == l_s) return 2.0 / (2.0 - rho * rho);
+  return 4.0 / (4.0 - rho * rho * nu_prev);
+}
+
+// v** -> v^{l+1}; vp is this row's v^{l-1} (read only when accelerating).
+template <typename T>
+__device__ __forceinline__ Vec4<T> cheb_combine(const ChebStep<T>& c, const Vec4<T>& vss,
+                                                const Vec4<T>& vl, const Vec4<T>* vp_ptr) {
+  if (!c.on) return vss;
+  Vec4<T> o;
+  if (!c.accel) {   // nu = 1: the v^{l-1} terms cancel
+    o.x = vl.x + c.u * (vss.x - vl.x);
+    o.y = vl.y + c.u * (vss.y - vl.y);
+    o.z = vl.z + c.u * (vss.z - vl.z);
+  } else {
+    const Vec4<T> vp = ldv(vp_ptr);
+    o.x = c.nu * (c.u * (vss.x - vl.x) + vl.x - vp.x) + vp.x;
+    o.y = c.nu * (c.u * (vss.y - vl.y) + vl.y - vp.y) + vp.y;
+    o.z = c.nu * (c.u * (vss.z - vl.z) + vl.z - vp.z) + vp.z;
+  }
+  o.w = T(0);
+  return o;
+}
 
 // ---------------------------------------------------------------------------
 // loads
@@ -269,7 +310,7 @@ __device__ __forceinline__ void row_product_prefetch(const DevProblem<T>& P, int
 template <typename T>
 struct ContactRec {
   T R[9];
-  T mu, phi;
+  T mu, phi, omega;
 };
 
 template <typename T>
@@ -279,14 +320,16 @@ __device__ __forceinline__ ContactRec<T> load_contact(const DevProblem<T>& P, in
   for (int q = 0; q < 9; ++q) c.R[q] = __ldg(P.c_R + (int64_t)q * P.n_c + cs);
   c.mu = __ldg(P.c_mu + cs);
   c.phi = __ldg(P.c_phi + cs);
+  c.omega = __ldg(P.c_omega + cs);
   return c;
 }
 
 // Given the relative surrogate velocity r = v*_i - v*_j (v*_i for an
-// S-contact) and gamma, compute lambda* and lambda.
+// S-contact) and gamma' = gamma + omega (eq. diagonal, eq. invt), compute
+// lambda* and lambda = ProjectFC(lambda*) (Alg. 2).
 template <typename T>
 __device__ __forceinline__ void one_shot(const ContactRec<T>& c, T gamma, T rx, T ry, T rz,
-                                         Vec4<T>& ls, Vec4<T>& lam) {
+                                         Vec4<T>& ls, Vec4<T>& lam, int prox) {
   // eta = R r  (eq. subp, J_{c,m} v*)
   const T en = c.R[0] * rx + c.R[1] * ry + c.R[2] * rz;
   const T e1 = c.R[3] * rx + c.R[4] * ry + c.R[5] * rz;
@@ -296,15 +339,30 @@ __device__ __forceinline__ void one_shot(const ContactRec<T>& c, T gamma, T rx, 
   ls.y = -e1 / gamma;
   ls.z = -e2 / gamma;
   ls.w = T(0);
-  // strict operator: normal clamp, then projection onto the disk mu*lambda_n
-  const T ln = ls.x > T(0) ? ls.x : T(0);
   const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
-  const T rad = c.mu * ln;
-  const T s = (rho <= rad) ? T(1) : rad / rho;
-  lam.x = ln;
-  lam.y = s * ls.y;
-  lam.z = s * ls.z;
   lam.w = T(0);
+  if (!prox) {
+    // strict operator: normal clamp, then projection onto the disk mu*lambda_n
+    const T ln = ls.x > T(0) ? ls.x : T(0);
+    const T rad = c.mu * ln;
+    const T s = (rho <= rad) ? T(1) : rad / rho;
+    lam.x = ln;
+    lam.y = s * ls.y;
+    lam.z = s * ls.z;
+  } else {
+    // proximal operator: Euclidean projection onto the friction cone
+    if (rho <= c.mu * ls.x) {
+      lam.x = ls.x; lam.y = ls.y; lam.z = ls.z;
+    } else if (c.mu * rho <= -ls.x) {
+      lam.x = T(0); lam.y = T(0); lam.z = T(0);
+    } else {
+      const T ln = (ls.x + c.mu * rho) / (T(1) + c.mu * c.mu);
+      const T s = c.mu * ln / rho;
+      lam.x = ln;
+      lam.y = s * ls.y;
+      lam.z = s * ls.z;
+    }
+  }
 }
 
 // R^T lambda
@@ -317,32 +375,52 @@ __device__ __forceinline__ void rt_lambda(const ContactRec<T>& c, const Vec4<T>&
 }
 
 // Adjoint of the contact step at a frozen active set.  With
-// S = W J^T P' Gamma^{-1} J (P' the Jacobian of the strict operator at the
-// frozen lambda*), the transpose iteration on u = W (I - S^T) g_bar reads
-// u_new = u* - (1/gamma) W J^T P'^T J u*; for one contact, z = R (u*_i - u*_j)
-// and q = P'^T z.  Returns q; also dL/dphi = -q_n / gamma and
-// dL/dmu = lambda_n t . z_t (slip only).
+// S = W J^T P' Gamma'^{-1} J (P' the Jacobian of ProjectFC at the frozen
+// lambda*, Gamma' = Gamma + Omega), the transpose iteration on
+// u = W (I - S^T) g_bar reads u_new = u* - (1/gamma') W J^T P'^T J u*; for one
+// contact, z = R (u*_i - u*_j) and q = P'^T z.  Returns q; also
+// dL/dphi = -q_n / gamma' and dL/dmu = z . dProjectFC/dmu.
 template <typename T>
 __device__ __forceinline__ void adjoint_step(const ContactRec<T>& c, const Vec4<T>& ls, T gamma,
-                                             T rx, T ry, T rz, Vec4<T>& q, T& gphi, T& gmu) {
+                                             T rx, T ry, T rz, Vec4<T>& q, T& gphi, T& gmu,
+                                             int prox) {
   const T zn = c.R[0] * rx + c.R[1] * ry + c.R[2] * rz;
   const T z1 = c.R[3] * rx + c.R[4] * ry + c.R[5] * rz;
   const T z2 = c.R[6] * rx + c.R[7] * ry + c.R[8] * rz;
   q = Vec4<T>{T(0), T(0), T(0), T(0)};
   gmu = T(0);
-  const T ln = ls.x;
-  if (ln > T(0)) {
-    const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
-    if (rho <= c.mu * ln) {            // stick: P' = I
+  const T a = ls.x;
+  const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
+  if (!prox) {
+    if (a > T(0)) {
+      if (rho <= c.mu * a) {            // stick: P' = I
+        q.x = zn; q.y = z1; q.z = z2;
+      } else {                          // slip
+        const T t1 = ls.y / rho, t2 = ls.z / rho;
+        const T tz = t1 * z1 + t2 * z2;
+        const T kap = c.mu * a / rho;
+        q.x = zn + c.mu * tz;
+        q.y = kap * (z1 - t1 * tz);
+        q.z = kap * (z2 - t2 * tz);
+        gmu = a * tz;
+      }
+    }
+  } else {
+    if (rho <= c.mu * a) {              // inside the cone: P' = I
       q.x = zn; q.y = z1; q.z = z2;
-    } else {                            // slip
+    } else if (!(c.mu * rho <= -a)) {   // on the cone's surface (polar cone: 0)
       const T t1 = ls.y / rho, t2 = ls.z / rho;
       const T tz = t1 * z1 + t2 * z2;
+      const T k = T(1) + c.mu * c.mu;
+      const T ln = (a + c.mu * rho) / k;
       const T kap = c.mu * ln / rho;
-      q.x = zn + c.mu * tz;
-      q.y = kap * (z1 - t1 * tz);
-      q.z = kap * (z2 - t2 * tz);
-      gmu = ln * tz;
+      // P' = [dln; mu t dln + kap (I - t t^T)] with dln = [1, mu t] / k
+      const T w = (zn + c.mu * tz) / k;  // dln . z summed over the rows that carry dln
+      q.x = w;
+      q.y = c.mu * t1 * w + kap * (z1 - t1 * tz);
+      q.z = c.mu * t2 * w + kap * (z2 - t2 * tz);
+      const T dln_dmu = (rho * k - T(2) * c.mu * (a + c.mu * rho)) / (k * k);
+      gmu = zn * dln_dmu + (ln + c.mu * dln_dmu) * tz;
     }
   }
   gphi = -q.x / gamma;
@@ -361,7 +439,8 @@ __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
 // sweep (b is then dL/dv and the contact step is the frozen linear map).
 template <typename T, bool ADJ, bool PF = false>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
-                                            const Vec4<T>* vin, Vec4<T>* vout) {
+                                            const Vec4<T>* vin, Vec4<T>* vout,
+                                            const ChebStep<T>& ch) {
   T a0, a1, a2;
   if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
   else row_product(P, slice, lane, vin, a0, a1, a2);
@@ -377,25 +456,28 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
   vn.w = T(0);
   const int cs = __ldg(P.cslot + row);
   if (cs >= 0) {
-    if (__ldg(P.c_j + cs) >= 0) {  // D-contact: finish in phase 2
-      stv(vout + row, vn);
+    const int cj = __ldg(P.c_j + cs);
+    if (cj >= 0) {  // D-contact: stage v* and finish in phase 2
+      stv(P.dstar + 2 * cs + (row == cj ? 1 : 0), vn);
       return 0.0;
     }
     const ContactRec<T> c = load_contact(P, cs);
+    const T gam = ww.x + c.omega;                    // gamma = w_i (Prop. 3), + omega (eq. invt)
     if constexpr (ADJ) {
       Vec4<T> q;
       T gphi, gmu;
-      adjoint_step(c, ldv(P.adj_ls + cs), ww.x, vn.x, vn.y, vn.z, q, gphi, gmu);
+      adjoint_step(c, ldv(P.adj_ls + cs), gam, vn.x, vn.y, vn.z, q, gphi, gmu, P.prox);
       T dx, dy, dz;
       rt_lambda(c, q, dx, dy, dz);
-      vn.x -= dx;                                    // (w_i / gamma) = 1
-      vn.y -= dy;
-      vn.z -= dz;
+      const T f = ww.x / gam;
+      vn.x -= f * dx;
+      vn.y -= f * dy;
+      vn.z -= f * dz;
       P.adj_gphi[cs] = gphi;
       P.adj_gmu[cs] = gmu;
     } else {
       Vec4<T> ls, lam;
-      one_shot(c, ww.x, vn.x, vn.y, vn.z, ls, lam);   // gamma = w_i (Prop. 3)
+      one_shot(c, gam, vn.x, vn.y, vn.z, ls, lam, P.prox);
       T dx, dy, dz;
       rt_lambda(c, lam, dx, dy, dz);
       vn.x += ww.x * dx;                               // eq. (vup)
@@ -405,6 +487,7 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
       stv(P.lam_star + cs, ls);
     }
   }
+  if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, vout + row);
   stv(vout + row, vn);
   return sqdiff(vn, vo);
 }
@@ -412,17 +495,18 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
 // Phase 2: D-contact d between internal nodes i and j (both rows hold v*).
 template <typename T, bool ADJ>
 __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, const Vec4<T>* vin,
-                                            Vec4<T>* vout) {
+                                            Vec4<T>* vout, const ChebStep<T>& ch) {
   const int i = P.c_i[cs], j = P.c_j[cs];
-  const Vec4<T> si = ldv(vout + i), sj = ldv(vout + j);
+  const Vec4<T> si = ldv(P.dstar + 2 * cs), sj = ldv(P.dstar + 2 * cs + 1);
   const T wi = P.w[i].x, wj = P.w[j].x;
   const ContactRec<T> c = load_contact(P, cs);
-  const T gamma = wi + wj;                                 // eq. (diagonal), D-contact
+  const T gamma = wi + wj + c.omega;                       // eq. (diagonal), D-contact; eq. (invt)
   Vec4<T> ni, nj;
   if constexpr (ADJ) {
     Vec4<T> q;
     T gphi, gmu;
-    adjoint_step(c, ldv(P.adj_ls + cs), gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, q, gphi, gmu);
+    adjoint_step(c, ldv(P.adj_ls + cs), gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, q, gphi, gmu,
+                 P.prox);
     T dx, dy, dz;
     rt_lambda(c, q, dx, dy, dz);
     const T fi = wi / gamma, fj = wj / gamma;
@@ -432,7 +516,7 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
     P.adj_gmu[cs] = gmu;
   } else {
     Vec4<T> ls, lam;
-    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam);
+    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam, P.prox);
     T dx, dy, dz;
     rt_lambda(c, lam, dx, dy, dz);
     ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
@@ -440,9 +524,14 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
     stv(P.lam + cs, lam);
     stv(P.lam_star + cs, ls);
   }
+  const Vec4<T> oi = ldv(vin + i), oj = ldv(vin + j);
+  if constexpr (!ADJ) {
+    ni = cheb_combine(ch, ni, oi, vout + i);
+    nj = cheb_combine(ch, nj, oj, vout + j);
+  }
   stv(vout + i, ni);
   stv(vout + j, nj);
-  return sqdiff(ni, ldv(vin + i)) + sqdiff(nj, ldv(vin + j));
+  return sqdiff(ni, oi) + sqdiff(nj, oj);
 }
 
 // ---------------------------------------------------------------------------
@@ -517,16 +606,22 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-  double theta = 0.0;
+  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
+    ChebStep<T> ch;
+    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.accel = ch.on && l >= ctl.cheb_ls;
+    ch.nu = (T)nu;
+    ch.u = (T)ctl.cheb_u;
     double acc = 0.0;
-    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout);
+    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout, ch);
     if (ctl.n_d > 0) {
       if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
       for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
-        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout);
+        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
     acc = block_allreduce<NT>(acc, red);
     double* part = ctl.partials + (l & 1) * gridDim.x;
@@ -540,6 +635,10 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
     if (theta < ctl.theta_th) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+    // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
+    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+    th2 = th1;
+    th1 = theta;
   }
   if (st != ST_TIMEOUT && cur == 1) {
     // the latest iterate lives in v1: copy the rows this warp owns into v0
@@ -575,22 +674,31 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
     const double nscale = ctl.norm_scale[sc];
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-    double theta = 0.0;
+    double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
     for (;; ++l) {
       const Vec4<T>* vin = cur ? P.v1 : P.v0;
       Vec4<T>* vout = cur ? P.v0 : P.v1;
+      ChebStep<T> ch;
+      ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+      nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+      ch.accel = ch.on && l >= ctl.cheb_ls;
+      ch.nu = (T)nu;
+      ch.u = (T)ctl.cheb_u;
       double acc = 0.0;
-      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout);
+      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout, ch);
       if (d1 > d0) {
         __syncthreads();
         for (int d = d0 + threadIdx.x; d < d1; d += NT)
-          acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout);
+          acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
       }
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;
       if (!isfinite(theta)) { st = ST_NONFINITE; break; }
       if (theta < ctl.theta_th) { st = ST_OK; break; }
       if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+      if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+      th2 = th1;
+      th1 = theta;
     }
     if (cur == 1) {
       for (int s = s0 + wid; s < s1; s += NT / 32) {

@@ -65,8 +65,9 @@ struct vfpi_ctx {
   int32_t* d_row_ptr = nullptr;             // caller's row pointers (value updates)
   double* d_ds = nullptr;                   // per-DOF row statistics for W
   int32_t *d_ci = nullptr, *d_cj = nullptr, *d_cperm = nullptr, *d_dlist = nullptr;
-  void *d_cR = nullptr, *d_cmu = nullptr, *d_cphi = nullptr;
+  void *d_cR = nullptr, *d_cmu = nullptr, *d_cphi = nullptr, *d_comega = nullptr;
   void *d_lam = nullptr, *d_lam_star = nullptr;
+  void* d_dstar = nullptr;                  // D-contact v* staging [2 n_c]
   int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
   double* d_norm_scale = nullptr;
   double* d_partials = nullptr;

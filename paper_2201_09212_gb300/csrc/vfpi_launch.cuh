@@ -28,9 +28,12 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.c_R = static_cast<const T*>(c->d_cR);
   P.c_mu = static_cast<const T*>(c->d_cmu);
   P.c_phi = static_cast<const T*>(c->d_cphi);
+  P.c_omega = static_cast<const T*>(c->d_comega);
+  P.prox = c->opts.operator_ == VFPI_OP_PROXIMAL ? 1 : 0;
   P.lam = static_cast<Vec4<T>*>(c->d_lam);
   P.lam_star = static_cast<Vec4<T>*>(c->d_lam_star);
   P.d_list = c->d_dlist;
+  P.dstar = static_cast<Vec4<T>*>(c->d_dstar);
   P.v0 = static_cast<Vec4<T>*>(c->d_v0);
   P.v1 = static_cast<Vec4<T>*>(c->d_v1);
   P.adj_ls = static_cast<const Vec4<T>*>(c->d_adj_ls);
@@ -232,6 +235,8 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.theta = c->d_theta;
   ctl.n_d = c->n_d;
   ctl.err = c->d_err;
+  ctl.cheb_ls = adjoint ? 0 : c->opts.chebyshev_ls;
+  ctl.cheb_u = c->opts.chebyshev_u;
   // control words: barrier count/generation, error flag, scene queue
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;

@@ -24,13 +24,15 @@ STATUS_NAMES = {0: "VFPI_OK", 1: "VFPI_NOT_CONVERGED", -1: "VFPI_ERR_INVALID_ARG
 DTYPES = {"f32": (0, np.float32), "f64": (1, np.float64)}
 W_MODES = {"frobenius": 0, "scalar": 1, "user": 2}
 NORMS = {"abs": 0, "rms": 1}
+OPERATORS = {"strict": 0, "proximal": 1}
 
 EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_velocity", "vfpi_get_velocity", "vfpi_get_lambda", "vfpi_get_w",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
-            "vfpi_configure_launch", "vfpi_set_tolerance",
+            "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
+            "vfpi_set_regularization",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
             "vfpi_noalloc_last_error")
 
@@ -57,7 +59,8 @@ class _Opts(C.Structure):
                 ("operator_", C.c_int32), ("residual_norm", C.c_int32), ("n_scenes", C.c_int32),
                 ("scene_ptr", C.c_void_p), ("block_threads", C.c_int32),
                 ("force_path", C.c_int32), ("kernel_variant", C.c_int32),
-                ("grid_ctas", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("grid_ctas", C.c_int32), ("chebyshev_ls", C.c_int32),
+                ("chebyshev_u", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 _LIB = None
@@ -98,6 +101,8 @@ def lib():
         "vfpi_last_kernel_ms": (st, [vp, vp]),
         "vfpi_configure_launch": (st, [vp, i32, i32, i32]),
         "vfpi_set_tolerance": (st, [vp, C.c_double, i32]),
+        "vfpi_set_chebyshev": (st, [vp, i32, C.c_double]),
+        "vfpi_set_regularization": (st, [vp, vp]),
         "vfpi_get_layout": (st, [vp, vp]),
         "vfpi_last_error": (C.c_char_p, [vp]),
         "vfpi_status_string": (C.c_char_p, [st]),
@@ -163,7 +168,8 @@ class Solver:
     def __init__(self, row_ptr, col_idx, vals, b, node_i, node_j, R, mu, phi, *, h=1e-3,
                  dtype="f32", w_mode="frobenius", alpha=0.0, w_user=None, theta_th=1e-5,
                  l_max=200, norm="abs", scene_ptr=None, block_threads=0, force_path=0,
-                 kernel_variant=0, grid_ctas=0, stream=None):
+                 kernel_variant=0, grid_ctas=0, chebyshev_ls=0, chebyshev_u=1.0,
+                 operator="strict", stream=None):
         self._L = lib()
         self.dtype_code, self.np_dtype = DTYPES[dtype]
         self.n_nodes = int(len(row_ptr) - 1)
@@ -186,12 +192,15 @@ class Solver:
         o.theta_th = float(theta_th)
         o.l_max = int(l_max)
         o.residual_norm = NORMS[norm]
+        o.operator_ = OPERATORS[operator]
         o.n_scenes = self.n_scenes
         o.scene_ptr = k.ptr(scene_ptr, np.int32)
         o.block_threads = int(block_threads)
         o.force_path = int(force_path)
         o.kernel_variant = int(kernel_variant)
         o.grid_ctas = int(grid_ctas)
+        o.chebyshev_ls = int(chebyshev_ls)
+        o.chebyshev_u = float(chebyshev_u)
         self.h = float(h)
         self._theta_th, self._l_max = float(theta_th), int(l_max)
         self.stream = stream
@@ -377,6 +386,13 @@ class Solver:
     def set_tolerance(self, theta_th, l_max):
         self._check(self._L.vfpi_set_tolerance(self._h, float(theta_th), int(l_max)))
         self._theta_th, self._l_max = float(theta_th), int(l_max)
+
+    def set_regularization(self, omega=None):
+        k = _Keep()
+        self._check(self._L.vfpi_set_regularization(self._h, k.ptr(omega, self.np_dtype)))
+
+    def set_chebyshev(self, l_s, u=1.0):
+        self._check(self._L.vfpi_set_chebyshev(self._h, int(l_s), float(u)))
 
     def layout(self) -> dict:
         info = (C.c_int64 * 8)()

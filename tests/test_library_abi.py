@@ -48,9 +48,9 @@ def test_struct_layout_matches_header(tmp_path):
         #include "vfpi.h"
         int main(void) {
           printf("%zu %zu %zu\\n", sizeof(vfpi_bsr), sizeof(vfpi_contacts), sizeof(vfpi_opts));
-          printf("%zu %zu %zu %zu %zu\\n", offsetof(vfpi_opts, theta_th), offsetof(vfpi_opts, l_max),
+          printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(vfpi_opts, theta_th), offsetof(vfpi_opts, l_max),
                  offsetof(vfpi_opts, scene_ptr), offsetof(vfpi_opts, force_path),
-                 offsetof(vfpi_contacts, phi));
+                 offsetof(vfpi_contacts, phi), offsetof(vfpi_opts, chebyshev_u));
           return 0;
         }"""))
     exe = tmp_path / "layout"
@@ -65,6 +65,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert sizes[5] == vfpi._Opts.scene_ptr.offset
     assert sizes[6] == vfpi._Opts.force_path.offset
     assert sizes[7] == vfpi._Contacts.phi.offset
+    assert sizes[8] == vfpi._Opts.chebyshev_u.offset
 
 
 def test_host_only_entry_points(L):
@@ -81,9 +82,13 @@ def test_host_only_entry_points(L):
     assert L.vfpi_create(C.byref(bsr), C.c_void_p(1), None, C.c_double(1e-3), C.byref(o), None,
                          C.byref(h)) == -1
     o.l_max = 10
-    o.operator_ = 1
+    o.operator_ = 5
     assert L.vfpi_create(C.byref(bsr), C.c_void_p(1), None, C.c_double(1e-3), C.byref(o), None,
-                         C.byref(h)) == -7
+                         C.byref(h)) == -1
+    o.operator_ = 0
+    o.chebyshev_ls = 2
+    assert L.vfpi_create(C.byref(bsr), C.c_void_p(1), None, C.c_double(1e-3), C.byref(o), None,
+                         C.byref(h)) == -1
     assert L.vfpi_step(None, None) == -1
     L.vfpi_destroy(None)
 

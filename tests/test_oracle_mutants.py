@@ -15,7 +15,9 @@ import pytest
 
 import oracle.vfpi as ov
 import oracle.adjoint as oadj
+import oracle.delassus as odel
 from tests import test_oracle_chebyshev as cheb
+from tests import test_oracle_proximal as prox
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -40,6 +42,10 @@ MUTANTS = {
     "adjoint_no_transpose": (oadj, "adjoint", "np.linalg.solve((np.eye(n) - D).T,",
                              "np.linalg.solve((np.eye(n) - D),"),
     "adjoint_mu_sign": (oadj, "strict_jacobian", "dmu[1:] = ln * t", "dmu[1:] = -ln * t"),
+    "prox_jac_kappa": (oadj, "proximal_jacobian", "Pp[1:, 1:] += mu * (ln / r) * (np.eye(2) - np.outer(t, t))",
+                       "Pp[1:, 1:] += (ln / r) * (np.eye(2) - np.outer(t, t))"),
+    "omega_sign": (ov, "sweep", "Gam = Gam + omega", "Gam = Gam - 0.5 * omega"),
+    "ccp_no_phi": (odel, "ccp_apgd", "q[0::3] += P.phi", "q[0::3] += 0.0 * P.phi"),
     "cheby_nu_first": (ov, "chebyshev_nu", "return 2.0 / (2.0 - rho * rho)", "return 2.0 / (2.0 - rho)"),
     "cheby_nu_rec": (ov, "chebyshev_nu", "return 4.0 / (4.0 - rho * rho * nu_prev)",
                      "return 4.0 / (4.0 - rho * nu_prev)"),
@@ -71,6 +77,9 @@ def _pin_suite():
         lambda: cheb.test_nu_schedule_is_the_chebyshev_polynomial_ratio(),
         lambda: cheb.test_same_fixed_point_and_fewer_iterations(0.9),
         lambda: cheb.test_fixed_rho_is_the_textbook_chebyshev_semi_iteration(),
+        lambda: prox.test_proximal_jacobian_matches_finite_differences(rng()),
+        lambda: prox.test_proximal_fixed_point_is_the_ccp_solution(0, True),
+        lambda: prox.test_invertible_model_recovers_impulse_from_velocity(ov.STRICT, rng()),
     ]
     for call in calls:
         try:
@@ -91,10 +100,10 @@ def test_pins_catch_planted_mistake(name, monkeypatch):
     exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
     monkeypatch.setattr(module, fname, ns[fname])
     monkeypatch.setattr(pins, fname, ns[fname], raising=False)
+    monkeypatch.setattr(prox, fname, ns[fname], raising=False)
     if module is ov:
         # functions imported by name elsewhere in the oracle follow the mutant
         monkeypatch.setattr(oadj, fname, ns[fname], raising=False)
-        import oracle.delassus as odel
         monkeypatch.setattr(odel, fname, ns[fname], raising=False)
     assert not _pin_suite(), f"no pin caught the planted mistake {name!r}"
 
