@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM traffic (read + write bytes per sweep) of the solve kernel, keyed by
 # the hash of the CUDA sources it was captured from; stale entries read as null.
-NCU_TRAFFIC = {"6824aeb57376cf2d": 553543394}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
+NCU_TRAFFIC = {"5b71db1b5c86f019": 553196126}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
 
 
 def source_hash() -> str:

@@ -83,3 +83,33 @@ def ccp_apgd(P, omega=None, iters: int = 200000, tol: float = 1e-15):
             break
     v = sla.cho_solve(chol, P.b + P.Jc.T @ lam)
     return v, lam.reshape(-1, 3), it
+
+
+def pgs_general(A, b, J, mu, phi, tol: float = 1e-14, max_sweeps: int = 200000):
+    """Projected Gauss-Seidel for ``A v = b + J^T lambda`` with an arbitrary
+    (not nodal) contact Jacobian ``J`` [3 n_c x n]: the original contact problem
+    that virtual nodes stand in for (Sec. III.A).  Dense."""
+    A = np.asarray(A, float)
+    J = np.asarray(J, float)
+    chol = sla.cho_factor(A)
+    G = J @ sla.cho_solve(chol, J.T)
+    c = J @ sla.cho_solve(chol, np.asarray(b, float))
+    n_c = J.shape[0] // 3
+    mu = np.asarray(mu, float)
+    g = np.array([np.linalg.eigvalsh(G[3 * m:3 * m + 3, 3 * m:3 * m + 3]).max() for m in range(n_c)])
+    lam = np.zeros(3 * n_c)
+    ph = np.zeros(3 * n_c)
+    ph[0::3] = phi
+    for _ in range(max_sweeps):
+        change = scale = 0.0
+        for m in range(n_c):
+            s = slice(3 * m, 3 * m + 3)
+            u = G[s] @ lam + c[s] + ph[s]
+            new = project_strict(lam[s] - u / g[m], mu[m:m + 1])[0]
+            change = max(change, float(np.abs(new - lam[s]).max()))
+            lam[s] = new
+            scale = max(scale, float(np.abs(new).max()))
+        if change <= tol * max(scale, 1e-300):
+            break
+    v = sla.cho_solve(chol, np.asarray(b, float) + J.T @ lam)
+    return v, lam.reshape(-1, 3)

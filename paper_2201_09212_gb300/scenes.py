@@ -568,3 +568,89 @@ def lattice_batch(n_scenes, *, seed, side_range=(4, 12), mass=1e-3, c=0.1, h=1e-
         scene_ptr=node_off.astype(np.int32),
         meta=dict(kind="lattice_batch", sides=sides, nodes=N_q, k=kk, coef=coef, gravity=grav,
                   node_mass=mass, seed=seed, dims=dims))
+
+
+# ----------------------------------------------------------------------------
+# virtual nodes (Sec. III.A, eq. vforce / eq. vnode) and rigid bodies
+# ----------------------------------------------------------------------------
+
+def skew(r) -> np.ndarray:
+    """Matrix of ``x -> r x x``."""
+    return np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]], [-r[1], r[0], 0.0]])
+
+
+def add_virtual_nodes(scene: Scene, jv_blocks, n_virtual: int, k_v: float, contacts,
+                      v_warm=None) -> Scene:
+    """Augment ``A_o v = b_o`` with ``n_virtual`` virtual nodes coupled by the
+    viscous force ``f_v = -k_v (J_v v - v_v)`` (eq. vforce):
+    ``A = [[A_o + k_v J_v^T J_v, -k_v J_v^T], [-k_v J_v, k_v I]]``,
+    ``b = [b_o; 0]`` (eq. vnode).
+
+    ``jv_blocks``: list of ``(p, i, B)`` -- virtual node p takes ``B v_i`` from
+    original node i (``J_v`` block row p).  ``contacts``: ``(node_i, node_j, R,
+    mu, phi)`` whose node indices may refer to virtual nodes as
+    ``scene.n_nodes + p``.  The warm start of a virtual node is ``J_v v``
+    (Sec. V.A).  Dense assembly: small systems only.
+    """
+    No, Nv = scene.n_nodes, n_virtual
+    N = No + Nv
+    A = np.zeros((3 * N, 3 * N))
+    A[:3 * No, :3 * No] = scene.dense_A()
+    Jv = np.zeros((3 * Nv, 3 * No))
+    for p, i, B in jv_blocks:
+        Jv[3 * p:3 * p + 3, 3 * i:3 * i + 3] += B
+    A[:3 * No, :3 * No] += k_v * Jv.T @ Jv
+    A[:3 * No, 3 * No:] = -k_v * Jv.T
+    A[3 * No:, :3 * No] = -k_v * Jv
+    A[3 * No:, 3 * No:] = k_v * np.eye(3 * Nv)
+    blocks = np.abs(A.reshape(N, 3, N, 3)).sum(axis=(1, 3)) > 0
+    row_ptr = np.zeros(N + 1, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(N):
+        js = np.nonzero(blocks[i])[0]
+        row_ptr[i + 1] = row_ptr[i] + len(js)
+        cols.extend(js)
+        vals.extend(A[3 * i:3 * i + 3, 3 * j:3 * j + 3] for j in js)
+    node_i, node_j, R, mu, phi = contacts
+    v_o = np.asarray(scene.v0 if v_warm is None else v_warm, dtype=np.float64)
+    v0 = np.concatenate([v_o, Jv @ v_o])
+    dt = scene.vals.dtype
+    return Scene(
+        n_nodes=N, row_ptr=row_ptr, col_idx=np.array(cols, dtype=np.int32),
+        vals=np.array(vals).reshape(-1, 3, 3).astype(dt),
+        b=np.concatenate([np.asarray(scene.b, float), np.zeros(3 * Nv)]).astype(dt),
+        node_i=np.asarray(node_i, dtype=np.int32), node_j=np.asarray(node_j, dtype=np.int32),
+        R=np.asarray(R, dtype=dt), mu=np.asarray(mu, dtype=dt), phi=np.asarray(phi, dtype=dt),
+        v0=v0.astype(dt), h=scene.h,
+        meta=dict(scene.meta, kind="virtual", k_v=k_v, n_original=No, Jv=Jv))
+
+
+def rigid_boxes(boxes, h=1e-3, gravity=(0.0, 0.0, -GRAVITY), dtype=np.float64):
+    """Rigid boxes as two nodes each (linear and angular velocity, 6 DOF), no
+    coupling: ``A = diag(m I, I_body)``, ``b = M v + h (m g + F, tau)``
+    (backward Euler without gyroscopic terms).  ``boxes``: dicts with ``m``,
+    ``size`` (3), ``v`` (6) and optional ``force`` (3, at the centre of mass)."""
+    N = 2 * len(boxes)
+    vals, b, v0 = [], [], []
+    g = np.asarray(gravity, float)
+    for bx in boxes:
+        m = bx["m"]
+        sx, sy, sz = bx["size"]
+        Ib = m / 12.0 * np.diag([sy * sy + sz * sz, sx * sx + sz * sz, sx * sx + sy * sy])
+        vals += [m * np.eye(3), Ib]
+        v = np.asarray(bx["v"], float)
+        F = np.asarray(bx.get("force", (0, 0, 0)), float)
+        b += [m * v[:3] + h * (m * g + F), Ib @ v[3:]]
+        v0 += [v[:3], v[3:]]
+    return Scene(
+        n_nodes=N, row_ptr=np.arange(N + 1, dtype=np.int32), col_idx=np.arange(N, dtype=np.int32),
+        vals=np.array(vals).astype(dtype), b=np.concatenate(b).astype(dtype),
+        node_i=np.zeros(0, np.int32), node_j=np.zeros(0, np.int32), R=np.zeros((0, 3, 3), dtype),
+        mu=np.zeros(0, dtype), phi=np.zeros(0, dtype), v0=np.concatenate(v0).astype(dtype), h=h,
+        meta=dict(kind="rigid", boxes=boxes))
+
+
+def point_jacobian(body: int, r) -> list:
+    """``J_v`` blocks of a point at offset ``r`` from body ``body``'s centre:
+    ``v_p = v - [r]x omega``."""
+    return [(None, 2 * body, np.eye(3)), (None, 2 * body + 1, -skew(r))]
