@@ -240,6 +240,25 @@ vfpi_status vfpi_set_tolerance(vfpi_t ctx, double theta_th, int32_t l_max);
  * the velocity alone.  Synchronises. */
 vfpi_status vfpi_set_regularization(vfpi_t ctx, const void* omega);
 
+/* Anisotropic friction (Sec. III.E): elliptic cones
+ * lambda_n^2 >= lambda_t1^2 / mu^2 + lambda_t2^2 / mu2^2 with mu along t1 (the
+ * contact's mu) and mu2 [n_c] along t2; the strict operator then projects
+ * lambda*_t onto the ellipse at lambda_n, the maximal-dissipation solution of
+ * Prop. 6 (a bounded bisection per contact).  NULL restores isotropic cones.
+ * Strict operator only; the adjoint of this model is not built
+ * (VFPI_ERR_UNSUPPORTED).  Synchronises. */
+vfpi_status vfpi_set_anisotropic_friction(vfpi_t ctx, const void* mu2);
+
+/* Barzilai-Borwein step sizes (Sec. IV.C) for later solves: W = alpha_l I with
+ * alpha_l = s^T s / s^T z (rule 1), s^T z / z^T z (rule 2) or the two
+ * alternating (rule 3: 1 on odd l, 2 on even), s = v^l - v^{l-1},
+ * z = A s = (A v^l - b) - (A v^{l-1} - b); alpha_1 = alpha0, and the previous
+ * alpha stays when s^T z <= 0.  Each sweep then has two phases around a grid
+ * barrier (the residual, then the update).  Rule 0 returns to the context's W.
+ * Excludes Chebyshev acceleration.  The adjoint's frozen active set must then
+ * be given explicitly (vfpi_adjoint's lambda_star). */
+vfpi_status vfpi_set_barzilai_borwein(vfpi_t ctx, int32_t rule, double alpha0);
+
 /* Chebyshev acceleration of later solves (Alg. 3, eq. chebyup, eq. varrho):
  * nu = 1 before the slow start l_s, 2 / (2 - rho^2) at l_s, then
  * 4 / (4 - rho^2 nu); v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}

@@ -126,6 +126,34 @@ def project_strict(lam_star: np.ndarray, mu: np.ndarray) -> np.ndarray:
     return lam
 
 
+def project_strict_elliptic(lam_star: np.ndarray, mu1: np.ndarray, mu2: np.ndarray) -> np.ndarray:
+    """Strict operator for the elliptic (anisotropic) cone
+    ``lambda_n^2 >= lambda_t1^2 / mu1^2 + lambda_t2^2 / mu2^2`` (Sec. III.E):
+    ``lambda_n = max(lambda*_n, 0)``, then ``lambda_t`` is the nearest point of
+    the ellipse with semi-axes ``mu1 lambda_n, mu2 lambda_n`` -- the maximal
+    dissipation solution (Prop. 6).  Outside the ellipse the nearest point is
+    ``t_k = a_k^2 t*_k / (a_k^2 + nu)`` with the multiplier ``nu > 0`` the root
+    of ``sum_k (a_k t*_k / (a_k^2 + nu))^2 = 1`` (found with brentq)."""
+    import scipy.optimize as so
+    lam_star = np.asarray(lam_star, dtype=np.float64).reshape(-1, 3)
+    lam = np.zeros_like(lam_star)
+    for m in range(lam_star.shape[0]):
+        ln = max(lam_star[m, 0], 0.0)
+        lam[m, 0] = ln
+        t = lam_star[m, 1:]
+        a = np.array([mu1[m], mu2[m]]) * ln
+        if ln == 0.0 or not np.any(a > 0):
+            continue
+        if (t[0] / a[0]) ** 2 + (t[1] / a[1]) ** 2 <= 1.0:
+            lam[m, 1:] = t
+            continue
+        g = lambda nu: np.sum((a * t / (a * a + nu)) ** 2) - 1.0
+        hi = np.sqrt(np.sum(a * a)) * np.linalg.norm(t)
+        nu = so.brentq(g, 0.0, hi, xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)
+        lam[m, 1:] = a * a * t / (a * a + nu)
+    return lam
+
+
 def project_proximal(lam_star: np.ndarray, mu: np.ndarray) -> np.ndarray:
     """Proximal operator: Euclidean projection onto the cone
     ``{lambda_n >= 0, ||lambda_t|| <= mu lambda_n}`` (eq. operator, eq. genfc)."""
@@ -169,11 +197,14 @@ class SweepResult:
 
 
 def sweep(P: Problem, w: np.ndarray, v: np.ndarray, operator: str = STRICT,
-          norm: str = NORM_ABS, omega: np.ndarray | None = None) -> SweepResult:
+          norm: str = NORM_ABS, omega: np.ndarray | None = None,
+          mu2: np.ndarray | None = None) -> SweepResult:
     """One V-FPI iteration from ``v = v^l``.
 
     ``omega`` (optional, [n_c, 3, 3]) is added to ``Gamma_c`` as in the
-    invertible-contact extension (eq. invt).
+    invertible-contact extension (eq. invt); ``mu2`` (optional, [n_c]) makes the
+    friction cone elliptic with coefficients ``mu`` along t1 and ``mu2`` along t2
+    (strict operator only, Prop. 6).
     """
     v = np.asarray(v, dtype=np.float64)
     # eq. (pgd1): gradient / surrogate-splitting step
@@ -187,7 +218,11 @@ def sweep(P: Problem, w: np.ndarray, v: np.ndarray, operator: str = STRICT,
     rhs = eta.copy()
     rhs[:, 0] += P.phi
     lam_star = -np.linalg.solve(Gam, rhs[:, :, None])[:, :, 0] if P.n_c else rhs
-    lam = (project_strict if operator == STRICT else project_proximal)(lam_star, P.mu)
+    if mu2 is not None:
+        assert operator == STRICT
+        lam = project_strict_elliptic(lam_star, P.mu, mu2)
+    else:
+        lam = (project_strict if operator == STRICT else project_proximal)(lam_star, P.mu)
     # eq. (vup): v^{l+1} = v* + W J_c^T lambda_c
     v_next = v_star + w * (P.Jc.T @ lam.ravel())
     dv = v_next - v
@@ -209,13 +244,13 @@ class SolveResult:
 
 
 def solve(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, l_max: int,
-          operator: str = STRICT, norm: str = NORM_ABS, omega=None) -> SolveResult:
+          operator: str = STRICT, norm: str = NORM_ABS, omega=None, mu2=None) -> SolveResult:
     """Alg. 1 inner loop: sweep, residual, break on ``theta < theta_th`` or ``l = l_max``."""
     v = np.asarray(v0, dtype=np.float64).copy()
     thetas = []
     l = 1
     while True:
-        r = sweep(P, w, v, operator, norm, omega)
+        r = sweep(P, w, v, operator, norm, omega, mu2)
         thetas.append(r.theta)
         if r.theta < theta_th or l == l_max:
             break
@@ -276,3 +311,43 @@ def solve_chebyshev(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, 
         v_prev, v = v, v_next
         l += 1
     return SolveResult(v_next, r.lam, r.lam_star, l, theta, theta < theta_th, thetas)
+
+
+# ----------------------------------------------------------------------------
+# Barzilai-Borwein step size (Sec. IV.C)
+# ----------------------------------------------------------------------------
+
+def bb_alpha(s: np.ndarray, z: np.ndarray, rule: str, alpha_prev: float) -> float:
+    """``alpha_bb1 = s^T s / s^T z`` or ``alpha_bb2 = s^T z / z^T z`` with
+    ``s = v^l - v^{l-1}`` and ``z = A s``; keeps the previous value when the
+    quotient is not a positive finite number (curvature s^T z <= 0)."""
+    ss = math.fsum(s * s)
+    sz = math.fsum(s * z)
+    zz = math.fsum(z * z)
+    a = ss / sz if rule == "bb1" else (sz / zz if zz > 0 else float("nan"))
+    return a if (sz > 0 and math.isfinite(a) and a > 0) else alpha_prev
+
+
+def solve_bb(P: Problem, v0: np.ndarray, theta_th: float, l_max: int, alpha0: float,
+             rule: str = "bb1", norm: str = NORM_ABS) -> SolveResult:
+    """Alg. 1 with the step matrix re-determined every iteration as
+    ``W = alpha_l I`` by the Barzilai-Borwein rule (``"bb1"``, ``"bb2"`` or
+    ``"alt"``, alternating bb1 on odd and bb2 on even l); ``alpha_1 = alpha0``.
+    A scalar W satisfies the tying of Prop. 3, so Alg. 2 stays one-shot."""
+    v = np.asarray(v0, dtype=np.float64).copy()
+    v_prev = r_prev = None
+    alpha = float(alpha0)
+    thetas = []
+    l = 1
+    while True:
+        r_l = P.A @ v - P.b
+        if v_prev is not None:
+            this = rule if rule != "alt" else ("bb1" if l % 2 == 1 else "bb2")
+            alpha = bb_alpha(v - v_prev, r_l - r_prev, this, alpha)
+        res = sweep(P, np.full(P.n, alpha), v, STRICT, norm)
+        thetas.append(res.theta)
+        if res.theta < theta_th or l == l_max:
+            break
+        v_prev, r_prev, v = v, r_l, res.v_next
+        l += 1
+    return SolveResult(res.v_next, res.lam, res.lam_star, l, res.theta, res.theta < theta_th, thetas)

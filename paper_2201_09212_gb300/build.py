@@ -18,8 +18,11 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libvfpi.so")
 UNITS = ("vfpi_f32", "vfpi_f64", "vfpi_api", "vfpi_noalloc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "--expt-relaxed-constexpr"]
+# -fmad=false: only the explicit fma() calls of the block-row product are fused,
+# so every launch shape and kernel variant evaluates the same IEEE operations in
+# source order (bitwise-identical iterates across shapes)
+FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
+         "-Wall", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

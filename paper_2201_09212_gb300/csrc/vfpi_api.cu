@@ -120,11 +120,12 @@ cudaError_t out_view(vfpi_ctx* c, void* dst, size_t bytes, size_t slot, void** o
 void free_all(vfpi_ctx* c) {
   void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_vals, c->d_cols, c->d_b, c->d_w,
                   c->d_v0, c->d_v1, c->d_t0, c->d_t1, c->d_cslot, c->d_node_map, c->d_row_ptr, c->d_ds,
-                  c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi, c->d_comega,
+                  c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2,
                   c->d_lam, c->d_lam_star, c->d_dstar, c->d_scene_slice, c->d_scene_d, c->d_order,
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
-                  c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_stage};
+                  c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
+                  c->d_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -241,7 +242,8 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   c->n_d = (int)dlist.size();
   int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist};
   for (auto p : ip) if (p) cudaFree(p);
-  void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_lam, c->d_lam_star, c->d_dstar};
+  void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2, c->d_lam, c->d_lam_star,
+                c->d_dstar};
   for (auto p : vp) if (p) cudaFree(p);
   VFPI_TRY_CUDA(dalloc(&c->d_ci, 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cj, 4 * (size_t)n_c));
@@ -251,6 +253,7 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(dalloc(&c->d_cmu, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cphi, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_comega, c->esz * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_cmu2, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam, c->esz * 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam_star, c->esz * 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_dstar, c->esz * 8 * (size_t)n_c));
@@ -261,6 +264,8 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_dlist, dlist.data(), 4 * dlist.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cR, Rint.data(), Rint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu2, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
+  c->aniso = 0;
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cphi, phint.data(), phint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_comega, 0, c->esz * (size_t)n_c, st));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_lam, 0, c->esz * 4 * (size_t)n_c, st));
@@ -623,6 +628,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
   CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
+  CREATE_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(cudaStreamSynchronize(st));
   if (c->stage_bytes > (64u << 20)) {  // the copy of a host-side A is no longer needed
     cudaFree(c->d_stage);
@@ -746,6 +752,11 @@ vfpi_status vfpi_adjoint(vfpi_t c, const void* lambda_star, const void* g_v, voi
                          void* g_phi, void* g_mu, int32_t* iters_out, double* theta_out) {
   CTX_CHECK(c);
   if (!g_v) return arg_fail(c, VFPI_ERR_INVALID_ARG, "g_v is NULL");
+  if (c->aniso)
+    return arg_fail(c, VFPI_ERR_UNSUPPORTED, "the adjoint of elliptic friction cones is not built");
+  if (c->bb_rule && !lambda_star)
+    return arg_fail(c, VFPI_ERR_UNSUPPORTED,
+                    "with Barzilai-Borwein steps pass lambda_star of a sweep with the context's W");
   const size_t vec = c->esz * 4 * (size_t)c->n_pad;
   if (!c->d_adj_g) {
     VFPI_TRY_CUDA(dalloc(&c->d_adj_g, vec));
@@ -906,8 +917,11 @@ vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t bloc
   }
   if (c->max_grid > old_max) {
     if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_bbpart) cudaFree(c->d_bbpart);
     c->d_partials = nullptr;
+    c->d_bbpart = nullptr;
     VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)c->max_grid));
+    VFPI_TRY_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)c->max_grid));
   }
   return VFPI_OK;
 }
@@ -962,10 +976,56 @@ vfpi_status vfpi_set_regularization(vfpi_t c, const void* omega) {
   return VFPI_OK;
 }
 
+vfpi_status vfpi_set_anisotropic_friction(vfpi_t c, const void* mu2) {
+  CTX_CHECK(c);
+  if (!mu2) {
+    c->aniso = 0;
+    return VFPI_OK;
+  }
+  if (c->opts.operator_ != VFPI_OP_STRICT)
+    return arg_fail(c, VFPI_ERR_UNSUPPORTED, "elliptic friction cones need the strict operator");
+  if (c->n_c == 0) return VFPI_OK;
+  std::vector<unsigned char> raw(c->esz * (size_t)c->n_c);
+  VFPI_TRY_CUDA(to_host(raw.data(), mu2, raw.size(), c->stream));
+  for (int m = 0; m < c->n_c; ++m) {
+    const double x = c->dtype == VFPI_F64 ? reinterpret_cast<const double*>(raw.data())[m]
+                                          : (double)reinterpret_cast<const float*>(raw.data())[m];
+    if (!(x >= 0) || !std::isfinite(x))
+      return arg_fail(c, VFPI_ERR_INVALID_ARG, "mu2 must be finite and >= 0");
+  }
+  const void* d;
+  VFPI_TRY_CUDA(device_view(c, mu2, raw.size(), 0, &d));
+  VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, d, c->d_cmu2, false)));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  c->aniso = 1;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_barzilai_borwein(vfpi_t c, int32_t rule, double alpha0) {
+  CTX_CHECK(c);
+  if (rule < 0 || rule > 3) return arg_fail(c, VFPI_ERR_INVALID_ARG, "rule must be 0..3");
+  if (rule && !(alpha0 > 0 && std::isfinite(alpha0)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "alpha0 must be > 0");
+  if (rule && c->opts.chebyshev_ls)
+    return arg_fail(c, VFPI_ERR_UNSUPPORTED, "Barzilai-Borwein steps and Chebyshev acceleration exclude each other");
+  if (rule && !c->d_r0) {
+    const size_t vec = c->esz * 4 * (size_t)c->n_pad;
+    VFPI_TRY_CUDA(dalloc(&c->d_r0, vec));
+    VFPI_TRY_CUDA(dalloc(&c->d_r1, vec));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_r0, 0, vec, c->stream));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_r1, 0, vec, c->stream));
+  }
+  c->bb_rule = rule;
+  c->bb_alpha0 = alpha0;
+  return VFPI_OK;
+}
+
 vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
   if (l_s != 0 && (l_s < 3 || !(u > 0 && u <= 1)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  if (l_s && c->bb_rule)
+    return arg_fail(c, VFPI_ERR_UNSUPPORTED, "Barzilai-Borwein steps and Chebyshev acceleration exclude each other");
   c->opts.chebyshev_ls = l_s;
   c->opts.chebyshev_u = u;
   return VFPI_OK;

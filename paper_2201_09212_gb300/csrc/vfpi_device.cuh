@@ -60,7 +60,9 @@ struct DevProblem {
   const T* c_mu;                 // [n_c]
   const T* c_phi;                // [n_c]
   const T* c_omega;              // [n_c] regularisation Omega_m = omega_m I (eq. invt)
+  const T* c_mu2;                // [n_c] friction along t2 of an elliptic cone
   int prox;                      // ProjectFC: 0 strict, 1 proximal (eq. operator)
+  int aniso;                     // elliptic friction cones (strict operator, Prop. 6)
   Vec4<T>* lam;                  // [n_c] lambda of the last sweep (n, t1, t2)
   Vec4<T>* lam_star;             // [n_c] lambda* of the last sweep
   const Vec4<T>* adj_ls;         // adjoint: frozen lambda* defining the active set
@@ -70,6 +72,8 @@ struct DevProblem {
   Vec4<T>* dstar;                // [2 n_c] v* of the two nodes of a D-contact
   Vec4<T>* v0;                   // ping-pong iterates
   Vec4<T>* v1;
+  Vec4<T>* r0;                   // Barzilai-Borwein: residuals A v^l - b of the
+  Vec4<T>* r1;                   //   current and previous sweep (ping-pong)
 };
 
 struct SolveCtl {
@@ -90,7 +94,19 @@ struct SolveCtl {
   int* err;                      // bit 0: a barrier wait ran out
   int32_t cheb_ls;               // Alg. 3 slow start l_s (0: plain Alg. 1)
   double cheb_u;                 // under-relaxation u
+  int32_t bb_rule;               // 0 off; W = alpha_l I with 1 bb1, 2 bb2, 3 alternating
+  double bb_alpha0;              // alpha_1
+  double* bb_part;               // [2][grid][3] FP64 partials of s.s, s.z, z.z (grid path)
 };
+
+// alpha_l from the three dot products (Sec. IV.C); the previous value stays
+// when the curvature s.z is not positive.
+__device__ __forceinline__ double bb_next(int rule, int l, double ss, double sz, double zz,
+                                          double prev) {
+  const int r = rule == 3 ? ((l & 1) ? 1 : 2) : rule;
+  const double a = r == 1 ? ss / sz : (zz > 0.0 ? sz / zz : -1.0);
+  return (sz > 0.0 && isfinite(a) && a > 0.0) ? a : prev;
+}
 
 // Chebyshev acceleration (Alg. 3): weight of the current sweep and the
 // combination v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}.
@@ -310,7 +326,7 @@ __device__ __forceinline__ void row_product_prefetch(const DevProblem<T>& P, int
 template <typename T>
 struct ContactRec {
   T R[9];
-  T mu, phi, omega;
+  T mu, phi, omega, mu2;
 };
 
 template <typename T>
@@ -321,7 +337,33 @@ __device__ __forceinline__ ContactRec<T> load_contact(const DevProblem<T>& P, in
   c.mu = __ldg(P.c_mu + cs);
   c.phi = __ldg(P.c_phi + cs);
   c.omega = __ldg(P.c_omega + cs);
+  c.mu2 = __ldg(P.c_mu2 + cs);
   return c;
+}
+
+// Nearest point of the ellipse t1^2/a1^2 + t2^2/a2^2 <= 1 to (t1, t2): outside
+// it, t_k = a_k^2 t_k / (a_k^2 + nu) with nu > 0 the root of
+// sum_k (a_k t_k / (a_k^2 + nu))^2 = 1, bracketed in [0, |a| |t|] and found by
+// bisection to the last representable bit (bounded loop).
+template <typename T>
+__device__ __forceinline__ void ellipse_project(T a1, T a2, T& t1, T& t2) {
+  const T A1 = a1 * a1, A2 = a2 * a2;
+  if (A1 == T(0) && A2 == T(0)) {   // frictionless
+    t1 = t2 = T(0);
+    return;
+  }
+  // inside (multiplied out; a zero semi-axis goes to the bisection, which
+  // handles the degenerate segment)
+  if (A1 > T(0) && A2 > T(0) && t1 * t1 * A2 + t2 * t2 * A1 <= A1 * A2) return;
+  T lo = T(0), hi = sqrt(A1 + A2) * sqrt(t1 * t1 + t2 * t2);
+  for (int it = 0; it < 200; ++it) {
+    const T mid = T(0.5) * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    const T f1 = a1 * t1 / (A1 + mid), f2 = a2 * t2 / (A2 + mid);
+    if (f1 * f1 + f2 * f2 > T(1)) lo = mid; else hi = mid;
+  }
+  t1 = A1 * t1 / (A1 + hi);
+  t2 = A2 * t2 / (A2 + hi);
 }
 
 // Given the relative surrogate velocity r = v*_i - v*_j (v*_i for an
@@ -341,7 +383,17 @@ __device__ __forceinline__ void one_shot(const ContactRec<T>& c, T gamma, T rx, 
   ls.w = T(0);
   const T rho = sqrt(ls.y * ls.y + ls.z * ls.z);
   lam.w = T(0);
-  if (!prox) {
+  if (prox == 2) {
+    // strict operator, elliptic cone: normal clamp, then the nearest point of
+    // the ellipse with semi-axes mu lambda_n, mu2 lambda_n (Prop. 6)
+    const T ln = ls.x > T(0) ? ls.x : T(0);
+    T t1 = ls.y, t2 = ls.z;
+    if (ln > T(0)) ellipse_project(c.mu * ln, c.mu2 * ln, t1, t2);
+    else t1 = t2 = T(0);
+    lam.x = ln;
+    lam.y = t1;
+    lam.z = t2;
+  } else if (!prox) {
     // strict operator: normal clamp, then projection onto the disk mu*lambda_n
     const T ln = ls.x > T(0) ? ls.x : T(0);
     const T rad = c.mu * ln;
@@ -477,7 +529,7 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
       P.adj_gmu[cs] = gmu;
     } else {
       Vec4<T> ls, lam;
-      one_shot(c, gam, vn.x, vn.y, vn.z, ls, lam, P.prox);
+      one_shot(c, gam, vn.x, vn.y, vn.z, ls, lam, P.aniso ? 2 : P.prox);
       T dx, dy, dz;
       rt_lambda(c, lam, dx, dy, dz);
       vn.x += ww.x * dx;                               // eq. (vup)
@@ -490,6 +542,82 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
   if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, vout + row);
   stv(vout + row, vn);
   return sqdiff(vn, vo);
+}
+
+// Barzilai-Borwein sweep, phase A: r_l = A v^l - b for this row (stored), and
+// the row's share of s.s, s.z, z.z with s = v^l - v^{l-1} (v^{l-1} is still in
+// the output buffer) and z = r_l - r_{l-1}.
+template <typename T>
+__device__ __forceinline__ void bb_residual_row(const DevProblem<T>& P, int slice, int lane,
+                                                const Vec4<T>* vin, const Vec4<T>* vold,
+                                                Vec4<T>* rcur, const Vec4<T>* rprev, bool first,
+                                                double& ss, double& sz, double& zz) {
+  T a0, a1, a2;
+  row_product(P, slice, lane, vin, a0, a1, a2);
+  const int row = slice * 32 + lane;
+  const Vec4<T> bb = ldv(P.b + row);
+  const Vec4<T> r = {a0 - bb.x, a1 - bb.y, a2 - bb.z, T(0)};
+  stv(rcur + row, r);
+  if (first) return;
+  const Vec4<T> vl = ldv(vin + row), vp = ldv(vold + row), rp = ldv(rprev + row);
+  const double s0 = (double)vl.x - vp.x, s1 = (double)vl.y - vp.y, s2 = (double)vl.z - vp.z;
+  const double z0 = (double)r.x - rp.x, z1 = (double)r.y - rp.y, z2 = (double)r.z - rp.z;
+  ss += s0 * s0 + s1 * s1 + s2 * s2;
+  sz += s0 * z0 + s1 * z1 + s2 * z2;
+  zz += z0 * z0 + z1 * z1 + z2 * z2;
+}
+
+// Phase B: v* = v^l - alpha r_l (eq. pgd1 with W = alpha I), then the contact
+// step as in sweep_row with gamma = alpha (+ omega).
+template <typename T>
+__device__ __forceinline__ double bb_update_row(const DevProblem<T>& P, int slice, int lane,
+                                                const Vec4<T>* vin, Vec4<T>* vout,
+                                                const Vec4<T>* rcur, T alpha) {
+  const int row = slice * 32 + lane;
+  const Vec4<T> vo = ldv(vin + row);
+  const Vec4<T> r = ldv(rcur + row);
+  Vec4<T> vn = {vo.x - alpha * r.x, vo.y - alpha * r.y, vo.z - alpha * r.z, T(0)};
+  const int cs = __ldg(P.cslot + row);
+  if (cs >= 0) {
+    const int cj = __ldg(P.c_j + cs);
+    if (cj >= 0) {
+      stv(P.dstar + 2 * cs + (row == cj ? 1 : 0), vn);
+      return 0.0;
+    }
+    const ContactRec<T> c = load_contact(P, cs);
+    Vec4<T> ls, lam;
+    one_shot(c, alpha + c.omega, vn.x, vn.y, vn.z, ls, lam, P.aniso ? 2 : P.prox);
+    T dx, dy, dz;
+    rt_lambda(c, lam, dx, dy, dz);
+    vn.x += alpha * dx;
+    vn.y += alpha * dy;
+    vn.z += alpha * dz;
+    stv(P.lam + cs, lam);
+    stv(P.lam_star + cs, ls);
+  }
+  stv(vout + row, vn);
+  return sqdiff(vn, vo);
+}
+
+// D-contact step with W = alpha I (gamma = 2 alpha + omega).
+template <typename T>
+__device__ __forceinline__ double bb_d_contact(const DevProblem<T>& P, int cs, const Vec4<T>* vin,
+                                               Vec4<T>* vout, T alpha) {
+  const int i = P.c_i[cs], j = P.c_j[cs];
+  const Vec4<T> si = ldv(P.dstar + 2 * cs), sj = ldv(P.dstar + 2 * cs + 1);
+  const ContactRec<T> c = load_contact(P, cs);
+  Vec4<T> ls, lam;
+  one_shot(c, alpha + alpha + c.omega, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam,
+           P.aniso ? 2 : P.prox);
+  T dx, dy, dz;
+  rt_lambda(c, lam, dx, dy, dz);
+  const Vec4<T> ni = {si.x + alpha * dx, si.y + alpha * dy, si.z + alpha * dz, T(0)};
+  const Vec4<T> nj = {sj.x - alpha * dx, sj.y - alpha * dy, sj.z - alpha * dz, T(0)};
+  stv(vout + i, ni);
+  stv(vout + j, nj);
+  stv(P.lam + cs, lam);
+  stv(P.lam_star + cs, ls);
+  return sqdiff(ni, ldv(vin + i)) + sqdiff(nj, ldv(vin + j));
 }
 
 // Phase 2: D-contact d between internal nodes i and j (both rows hold v*).
@@ -516,7 +644,7 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
     P.adj_gmu[cs] = gmu;
   } else {
     Vec4<T> ls, lam;
-    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam, P.prox);
+    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam, P.aniso ? 2 : P.prox);
     T dx, dy, dz;
     rt_lambda(c, lam, dx, dy, dz);
     ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
@@ -606,7 +734,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -617,11 +745,51 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
     double acc = 0.0;
-    for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout, ch);
-    if (ctl.n_d > 0) {
+    if (!ADJ && ctl.bb_rule) {
+      Vec4<T>* rcur = (l & 1) ? P.r1 : P.r0;
+      const Vec4<T>* rprev = (l & 1) ? P.r0 : P.r1;
+      double ss = 0.0, sz = 0.0, zz = 0.0;
+      for (int s = gw; s < P.n_slices; s += nw)
+        bb_residual_row(P, s, lane, vin, vout, rcur, rprev, l == 1, ss, sz, zz);
+      if (l > 1) {
+        ss = block_allreduce<NT>(ss, red);
+        sz = block_allreduce<NT>(sz, red);
+        zz = block_allreduce<NT>(zz, red);
+        double* bp = ctl.bb_part + (size_t)(l & 1) * 3 * gridDim.x;
+        if (threadIdx.x == 0) {
+          bp[3 * blockIdx.x] = ss;
+          bp[3 * blockIdx.x + 1] = sz;
+          bp[3 * blockIdx.x + 2] = zz;
+        }
+      }
       if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
-      for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
-        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+      if (l > 1) {
+        const double* bp = ctl.bb_part + (size_t)(l & 1) * 3 * gridDim.x;
+        double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) {
+          q0 += bp[3 * q];
+          q1 += bp[3 * q + 1];
+          q2 += bp[3 * q + 2];
+        }
+        q0 = block_allreduce<NT>(q0, red);
+        q1 = block_allreduce<NT>(q1, red);
+        q2 = block_allreduce<NT>(q2, red);
+        bb_alpha = bb_next(ctl.bb_rule, l, q0, q1, q2, bb_alpha);
+      }
+      for (int s = gw; s < P.n_slices; s += nw)
+        acc += bb_update_row(P, s, lane, vin, vout, rcur, (T)bb_alpha);
+      if (ctl.n_d > 0) {
+        if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+        for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
+          acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
+      }
+    } else {
+      for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout, ch);
+      if (ctl.n_d > 0) {
+        if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+        for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
+          acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+      }
     }
     acc = block_allreduce<NT>(acc, red);
     double* part = ctl.partials + (l & 1) * gridDim.x;
@@ -674,7 +842,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
     const double nscale = ctl.norm_scale[sc];
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-    double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+    double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
     for (;; ++l) {
       const Vec4<T>* vin = cur ? P.v1 : P.v0;
       Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -685,11 +853,30 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
       ch.nu = (T)nu;
       ch.u = (T)ctl.cheb_u;
       double acc = 0.0;
-      for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout, ch);
-      if (d1 > d0) {
-        __syncthreads();
-        for (int d = d0 + threadIdx.x; d < d1; d += NT)
-          acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+      if (!ADJ && ctl.bb_rule) {
+        Vec4<T>* rcur = (l & 1) ? P.r1 : P.r0;
+        const Vec4<T>* rprev = (l & 1) ? P.r0 : P.r1;
+        double ss = 0.0, sz = 0.0, zz = 0.0;
+        for (int s = s0 + wid; s < s1; s += NT / 32)
+          bb_residual_row(P, s, lane, vin, vout, rcur, rprev, l == 1, ss, sz, zz);
+        ss = block_allreduce<NT>(ss, red);   // (also orders phase A before phase B)
+        sz = block_allreduce<NT>(sz, red);
+        zz = block_allreduce<NT>(zz, red);
+        if (l > 1) bb_alpha = bb_next(ctl.bb_rule, l, ss, sz, zz, bb_alpha);
+        for (int s = s0 + wid; s < s1; s += NT / 32)
+          acc += bb_update_row(P, s, lane, vin, vout, rcur, (T)bb_alpha);
+        if (d1 > d0) {
+          __syncthreads();
+          for (int d = d0 + threadIdx.x; d < d1; d += NT)
+            acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
+        }
+      } else {
+        for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout, ch);
+        if (d1 > d0) {
+          __syncthreads();
+          for (int d = d0 + threadIdx.x; d < d1; d += NT)
+            acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+        }
       }
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;

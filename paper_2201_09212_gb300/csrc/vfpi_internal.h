@@ -66,11 +66,17 @@ struct vfpi_ctx {
   double* d_ds = nullptr;                   // per-DOF row statistics for W
   int32_t *d_ci = nullptr, *d_cj = nullptr, *d_cperm = nullptr, *d_dlist = nullptr;
   void *d_cR = nullptr, *d_cmu = nullptr, *d_cphi = nullptr, *d_comega = nullptr;
+  void* d_cmu2 = nullptr;                   // friction along t2 (elliptic cones)
+  int aniso = 0;
   void *d_lam = nullptr, *d_lam_star = nullptr;
   void* d_dstar = nullptr;                  // D-contact v* staging [2 n_c]
   int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
   double* d_norm_scale = nullptr;
   double* d_partials = nullptr;
+  double* d_bbpart = nullptr;               // BB dot-product partials [2][max_grid][3]
+  void *d_r0 = nullptr, *d_r1 = nullptr;    // BB residual ping-pong (allocated on use)
+  int bb_rule = 0;
+  double bb_alpha0 = 0.0;
   unsigned int* d_bar = nullptr;
   int* d_err = nullptr;
   int32_t *d_iters = nullptr, *d_status = nullptr;

@@ -29,6 +29,8 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.c_mu = static_cast<const T*>(c->d_cmu);
   P.c_phi = static_cast<const T*>(c->d_cphi);
   P.c_omega = static_cast<const T*>(c->d_comega);
+  P.c_mu2 = static_cast<const T*>(c->d_cmu2);
+  P.aniso = c->aniso;
   P.prox = c->opts.operator_ == VFPI_OP_PROXIMAL ? 1 : 0;
   P.lam = static_cast<Vec4<T>*>(c->d_lam);
   P.lam_star = static_cast<Vec4<T>*>(c->d_lam_star);
@@ -36,6 +38,8 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.dstar = static_cast<Vec4<T>*>(c->d_dstar);
   P.v0 = static_cast<Vec4<T>*>(c->d_v0);
   P.v1 = static_cast<Vec4<T>*>(c->d_v1);
+  P.r0 = static_cast<Vec4<T>*>(c->d_r0);
+  P.r1 = static_cast<Vec4<T>*>(c->d_r1);
   P.adj_ls = static_cast<const Vec4<T>*>(c->d_adj_ls);
   P.adj_gphi = static_cast<T*>(c->d_adj_gphi);
   P.adj_gmu = static_cast<T*>(c->d_adj_gmu);
@@ -237,6 +241,9 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.err = c->d_err;
   ctl.cheb_ls = adjoint ? 0 : c->opts.chebyshev_ls;
   ctl.cheb_u = c->opts.chebyshev_u;
+  ctl.bb_rule = adjoint ? 0 : c->bb_rule;
+  ctl.bb_alpha0 = c->bb_alpha0;
+  ctl.bb_part = c->d_bbpart;
   // control words: barrier count/generation, error flag, scene queue
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;

@@ -32,7 +32,8 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
             "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
-            "vfpi_set_regularization",
+            "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
+            "vfpi_set_barzilai_borwein",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
             "vfpi_noalloc_last_error")
 
@@ -103,6 +104,8 @@ def lib():
         "vfpi_set_tolerance": (st, [vp, C.c_double, i32]),
         "vfpi_set_chebyshev": (st, [vp, i32, C.c_double]),
         "vfpi_set_regularization": (st, [vp, vp]),
+        "vfpi_set_anisotropic_friction": (st, [vp, vp]),
+        "vfpi_set_barzilai_borwein": (st, [vp, i32, C.c_double]),
         "vfpi_get_layout": (st, [vp, vp]),
         "vfpi_last_error": (C.c_char_p, [vp]),
         "vfpi_status_string": (C.c_char_p, [st]),
@@ -390,6 +393,15 @@ class Solver:
     def set_regularization(self, omega=None):
         k = _Keep()
         self._check(self._L.vfpi_set_regularization(self._h, k.ptr(omega, self.np_dtype)))
+
+    def set_anisotropic_friction(self, mu2=None):
+        k = _Keep()
+        self._check(self._L.vfpi_set_anisotropic_friction(self._h, k.ptr(mu2, self.np_dtype)))
+
+    def set_barzilai_borwein(self, rule, alpha0=0.0):
+        """rule: 0 off, "bb1"/1, "bb2"/2, "alt"/3."""
+        rule = {"bb1": 1, "bb2": 2, "alt": 3, None: 0}.get(rule, rule)
+        self._check(self._L.vfpi_set_barzilai_borwein(self._h, int(rule), float(alpha0)))
 
     def set_chebyshev(self, l_s, u=1.0):
         self._check(self._L.vfpi_set_chebyshev(self._h, int(l_s), float(u)))

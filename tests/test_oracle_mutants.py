@@ -18,6 +18,8 @@ import oracle.adjoint as oadj
 import oracle.delassus as odel
 from tests import test_oracle_chebyshev as cheb
 from tests import test_oracle_proximal as prox
+from tests import test_oracle_bb as bbt
+from tests import test_oracle_anisotropic as ani
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -46,6 +48,11 @@ MUTANTS = {
                        "Pp[1:, 1:] += (ln / r) * (np.eye(2) - np.outer(t, t))"),
     "omega_sign": (ov, "sweep", "Gam = Gam + omega", "Gam = Gam - 0.5 * omega"),
     "ccp_no_phi": (odel, "ccp_apgd", "q[0::3] += P.phi", "q[0::3] += 0.0 * P.phi"),
+    "bb1_inverted": (ov, "bb_alpha", 'a = ss / sz if rule == "bb1"', 'a = sz / ss if rule == "bb1"'),
+    "bb_residual_lag": (ov, "solve_bb", "v_prev, r_prev, v = v, r_l, res.v_next",
+                        "v_prev, r_prev, v = v, P.A @ res.v_next - P.b, res.v_next"),
+    "elliptic_axes_swapped": (ov, "project_strict_elliptic", "a = np.array([mu1[m], mu2[m]]) * ln",
+                              "a = np.array([mu2[m], mu1[m]]) * ln"),
     "cheby_nu_first": (ov, "chebyshev_nu", "return 2.0 / (2.0 - rho * rho)", "return 2.0 / (2.0 - rho)"),
     "cheby_nu_rec": (ov, "chebyshev_nu", "return 4.0 / (4.0 - rho * rho * nu_prev)",
                      "return 4.0 / (4.0 - rho * nu_prev)"),
@@ -80,6 +87,9 @@ def _pin_suite():
         lambda: prox.test_proximal_jacobian_matches_finite_differences(rng()),
         lambda: prox.test_proximal_fixed_point_is_the_ccp_solution(0, True),
         lambda: prox.test_invertible_model_recovers_impulse_from_velocity(ov.STRICT, rng()),
+        lambda: bbt.test_bb_quotients_on_an_eigenvector(),
+        lambda: bbt.test_without_contacts_bb_is_the_textbook_gradient_method(),
+        lambda: ani.test_elliptic_projection_is_the_nearest_point(rng()),
     ]
     for call in calls:
         try:
