@@ -134,7 +134,13 @@ enum {
   VFPI_VARIANT_256_2_PF = 4,
   VFPI_VARIANT_128_4_PF = 5,
   VFPI_VARIANT_512_1_PF = 6,
-  VFPI_VARIANT_256_2 = 7
+  VFPI_VARIANT_256_2 = 7,
+  /* shared-memory staging: each warp streams its chunks through a ring of
+   * N stages filled by 1-D bulk copies (TMA) -- threads per CTA / stages */
+  VFPI_VARIANT_TMA_256_4 = 8,
+  VFPI_VARIANT_TMA_128_4 = 9,
+  VFPI_VARIANT_TMA_128_6 = 10,
+  VFPI_VARIANT_TMA_64_8 = 11
 };
 
 /* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,

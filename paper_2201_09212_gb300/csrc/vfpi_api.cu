@@ -614,16 +614,18 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
   if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   c->nt = o->block_threads ? o->block_threads : (c->path == 1 ? 256 : 128);
-  if (o->kernel_variant < 0 || o->kernel_variant > VFPI_VARIANT_256_2) {
+  if (o->kernel_variant < 0 || o->kernel_variant > VFPI_VARIANT_TMA_64_8) {
     c->err = "unknown kernel_variant";
     return fail(VFPI_ERR_INVALID_ARG);
   }
   if (c->path == 1 && (o->kernel_variant > 0 || !o->block_threads)) {
-    static const int table[8][3] = {{256, 3, 0}, {256, 4, 0}, {512, 2, 0}, {128, 8, 0},
-                                    {256, 2, 1}, {128, 4, 1}, {512, 1, 1}, {256, 2, 0}};
+    static const int table[12][4] = {{256, 3, 0, 0}, {256, 4, 0, 0}, {512, 2, 0, 0}, {128, 8, 0, 0},
+                                     {256, 2, 1, 0}, {128, 4, 1, 0}, {512, 1, 1, 0}, {256, 2, 0, 0},
+                                     {256, 1, 0, 4}, {128, 1, 0, 4}, {128, 1, 0, 6}, {64, 1, 0, 8}};
     c->nt = table[o->kernel_variant][0];
     c->minb = table[o->kernel_variant][1];
     c->pf = table[o->kernel_variant][2];
+    c->tma_stages = table[o->kernel_variant][3];
   }
   if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
@@ -889,29 +891,32 @@ vfpi_status vfpi_matvec(vfpi_t c, const void* x, void* y) {
 vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t block_threads,
                                   int32_t grid_ctas) {
   CTX_CHECK(c);
-  if (kernel_variant < 0 || kernel_variant > VFPI_VARIANT_256_2)
+  if (kernel_variant < 0 || kernel_variant > VFPI_VARIANT_TMA_64_8)
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "unknown kernel_variant");
   if (block_threads && block_threads != 64 && block_threads != 128 && block_threads != 256 &&
       block_threads != 512)
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
   if (grid_ctas < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "grid_ctas must be >= 0");
   VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
-  const int nt0 = c->nt, mb0 = c->minb, pf0 = c->pf, g0 = c->opts.grid_ctas;
+  const int nt0 = c->nt, mb0 = c->minb, pf0 = c->pf, tm0 = c->tma_stages, g0 = c->opts.grid_ctas;
   c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
   c->minb = 1;
   c->pf = 0;
+  c->tma_stages = 0;
   if (c->path == 1 && (kernel_variant > 0 || !block_threads)) {
-    static const int table[8][3] = {{256, 3, 0}, {256, 4, 0}, {512, 2, 0}, {128, 8, 0},
-                                    {256, 2, 1}, {128, 4, 1}, {512, 1, 1}, {256, 2, 0}};
+    static const int table[12][4] = {{256, 3, 0, 0}, {256, 4, 0, 0}, {512, 2, 0, 0}, {128, 8, 0, 0},
+                                     {256, 2, 1, 0}, {128, 4, 1, 0}, {512, 1, 1, 0}, {256, 2, 0, 0},
+                                     {256, 1, 0, 4}, {128, 1, 0, 4}, {128, 1, 0, 6}, {64, 1, 0, 8}};
     c->nt = table[kernel_variant][0];
     c->minb = table[kernel_variant][1];
     c->pf = table[kernel_variant][2];
+    c->tma_stages = table[kernel_variant][3];
   }
   c->opts.grid_ctas = grid_ctas;
   const int old_max = c->max_grid;
   cudaError_t e = DISPATCH(c, configure(c));
   if (e != cudaSuccess) {
-    c->nt = nt0; c->minb = mb0; c->pf = pf0; c->opts.grid_ctas = g0;
+    c->nt = nt0; c->minb = mb0; c->pf = pf0; c->tma_stages = tm0; c->opts.grid_ctas = g0;
     DISPATCH(c, configure(c));
     return cuda_fail(c, e, "configure");
   }

@@ -486,17 +486,14 @@ __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
   return dx * dx + dy * dy + dz * dz;
 }
 
-// One row of one sweep: returns this row's contribution to ||dv||^2 (0 for a
-// D-contact node, whose update happens in phase 2).  ADJ selects the adjoint
-// sweep (b is then dL/dv and the contact step is the frozen linear map).
-template <typename T, bool ADJ, bool PF = false>
-__device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
-                                            const Vec4<T>* vin, Vec4<T>* vout,
-                                            const ChebStep<T>& ch) {
-  T a0, a1, a2;
-  if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
-  else row_product(P, slice, lane, vin, a0, a1, a2);
-  const int row = slice * 32 + lane;
+// One row of one sweep after its block-row product (a0, a1, a2) = (A v)_row:
+// returns the row's contribution to ||dv||^2 (0 for a D-contact node, whose
+// update happens in phase 2).  ADJ selects the adjoint sweep (b is then dL/dv
+// and the contact step is the frozen linear map).
+template <typename T, bool ADJ>
+__device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T a0, T a1, T a2,
+                                             const Vec4<T>* vin, Vec4<T>* vout,
+                                             const ChebStep<T>& ch) {
   const Vec4<T> vo = ldv(vin + row);
   const Vec4<T> bb = ldv(P.b + row);
   const Vec4<T> ww = ldv(P.w + row);
@@ -542,6 +539,16 @@ __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, i
   if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, vout + row);
   stv(vout + row, vn);
   return sqdiff(vn, vo);
+}
+
+template <typename T, bool ADJ, bool PF = false>
+__device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
+                                            const Vec4<T>* vin, Vec4<T>* vout,
+                                            const ChebStep<T>& ch) {
+  T a0, a1, a2;
+  if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
+  else row_product(P, slice, lane, vin, a0, a1, a2);
+  return finish_row<T, ADJ>(P, slice * 32 + lane, a0, a1, a2, vin, vout, ch);
 }
 
 // Barzilai-Borwein sweep, phase A: r_l = A v^l - b for this row (stored), and
@@ -810,6 +817,254 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   }
   if (st != ST_TIMEOUT && cur == 1) {
     // the latest iterate lives in v1: copy the rows this warp owns into v0
+    for (int s = gw; s < P.n_slices; s += nw) {
+      const int row = s * 32 + lane;
+      stv(P.v0 + row, ldv(P.v1 + row));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl.iters[0] = l;
+    ctl.theta[0] = theta;
+    ctl.status[0] = st;
+  }
+  if (st == ST_TIMEOUT && threadIdx.x == 0) atomicOr(ctl.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged variant of the grid-wide solve
+// ---------------------------------------------------------------------------
+//
+// Each warp keeps a private ring of NST stages in shared memory.  A stage holds
+// one chunk of a slice (the VW-entry group of column indices and values, or the
+// slice's leftover entries), which the sliced-ELL layout stores as two
+// contiguous, 16-byte aligned byte ranges; lane 0 moves them with two 1-D bulk
+// copies (cp.async.bulk, the TMA engine) that complete on the stage's mbarrier,
+// and refills a stage as soon as the warp has consumed it, so NST - 1 chunks per
+// warp are always in flight while the lanes gather v and do the FMAs from
+// shared memory.  Every wait is bounded; on a timeout the warp drains its own
+// copies (bounded too), flags the error and the kernel stops.
+
+constexpr long long kMbarPolls = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the copy did not land within the poll budget
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kMbarPolls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+struct TmaGeom {
+  static constexpr int VW = Chunk<T>::VW;
+  static constexpr uint32_t kVals = 288u * VW * sizeof(T);   // one chunk's values
+  static constexpr uint32_t kCols = 32u * VW * 4u;           // one chunk's column indices
+  static constexpr uint32_t kStage = kVals + kCols;          // multiple of 16
+};
+
+template <typename T, int NT, int NST>
+constexpr size_t tma_smem_bytes() {
+  return 128 * (((NT / 32) * NST * 8 + 127) / 128) + (size_t)(NT / 32) * NST * TmaGeom<T>::kStage;
+}
+
+// Cursor over one warp's chunk stream: slices gw, gw + nw, ..., each split in
+// its full chunks and (if any) its leftover entries.
+struct TmaCursor {
+  int s, k;
+};
+
+template <typename T>
+__device__ __forceinline__ bool tma_issue(const DevProblem<T>& P, TmaCursor& cur, int nw, int lane,
+                                          unsigned char* stage, uint64_t* bar) {
+  using G = TmaGeom<T>;
+  while (cur.s < P.n_slices) {
+    const int len = P.slice_len[cur.s];
+    const int nfull = len / G::VW, ntail = len - nfull * G::VW;
+    const int nitems = nfull + (ntail > 0 ? 1 : 0);
+    if (cur.k < nitems) {
+      const int64_t off = P.slice_off[cur.s];
+      const bool full = cur.k < nfull;
+      const uint32_t vb = full ? G::kVals : (uint32_t)(ntail * 288 * sizeof(T));
+      const uint32_t cb = full ? G::kCols : (uint32_t)(ntail * 128);
+      if (lane == 0) {
+        const T* vsrc = P.vals + off * 288 + (int64_t)cur.k * (288 * G::VW);
+        const int32_t* csrc = P.cols + off * 32 + (int64_t)cur.k * (32 * G::VW);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, vb + cb);
+        bulk_g2s(stage, vsrc, vb, bar);
+        bulk_g2s(stage + G::kVals, csrc, cb, bar);
+      }
+      if (++cur.k >= nitems) {
+        cur.k = 0;
+        cur.s += nw;
+      }
+      return true;
+    }
+    cur.k = 0;
+    cur.s += nw;
+  }
+  return false;
+}
+
+template <typename T, int NT, int NST, bool ADJ>
+__global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, SolveCtl ctl) {
+  using G = TmaGeom<T>;
+  constexpr int NW = NT / 32;
+  constexpr int VW = G::VW;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ double red[33];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * NW + wib, nw = gridDim.x * NW;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm) + wib * NST;
+  unsigned char* ring = dsm + 128 * ((NW * NST * 8 + 127) / 128) + (size_t)wib * NST * G::kStage;
+  if (lane == 0) {
+    for (int q = 0; q < NST; ++q) mbar_init(bars + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  uint32_t phase = 0;  // bit q: parity of the next completion of stage q
+  int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+  bool failed = false;
+  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  for (;; ++l) {
+    const Vec4<T>* vin = cur ? P.v1 : P.v0;
+    Vec4<T>* vout = cur ? P.v0 : P.v1;
+    ChebStep<T> ch;
+    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.accel = ch.on && l >= ctl.cheb_ls;
+    ch.nu = (T)nu;
+    ch.u = (T)ctl.cheb_u;
+    double acc = 0.0;
+    // the warp's chunk stream for this sweep: prefill the ring, then consume
+    TmaCursor pc{gw, 0};
+    int issued = 0, consumed = 0;
+    for (int q = 0; q < NST; ++q)
+      if (tma_issue(P, pc, nw, lane, ring + (size_t)(issued % NST) * G::kStage, bars + issued % NST))
+        ++issued;
+    for (int s = gw; s < P.n_slices && !failed; s += nw) {
+      const int len = P.slice_len[s];
+      const int nfull = len / VW, ntail = len - nfull * VW;
+      const int nitems = nfull + (ntail > 0 ? 1 : 0);
+      T a0 = T(0), a1 = T(0), a2 = T(0);
+      for (int k = 0; k < nitems; ++k) {
+        const int sg = consumed % NST;
+        if (!mbar_wait(bars + sg, (phase >> sg) & 1u)) {
+          failed = true;
+          break;
+        }
+        phase ^= 1u << sg;
+        const unsigned char* stg = ring + (size_t)sg * G::kStage;
+        const T* sv = reinterpret_cast<const T*>(stg);
+        const int32_t* sc = reinterpret_cast<const int32_t*>(stg + G::kVals);
+        if (k < nfull) {
+          int c[VW];
+          T m[9][VW];
+          if constexpr (VW == 4) {
+            const int4 q4 = *reinterpret_cast<const int4*>(sc + lane * 4);
+            c[0] = q4.x; c[1] = q4.y; c[2] = q4.z; c[3] = q4.w;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+              const float4 f = *reinterpret_cast<const float4*>(sv + q * 128 + lane * 4);
+              m[q][0] = f.x; m[q][1] = f.y; m[q][2] = f.z; m[q][3] = f.w;
+            }
+          } else {
+            const int2 q2 = *reinterpret_cast<const int2*>(sc + lane * 2);
+            c[0] = q2.x; c[1] = q2.y;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+              const double2 f = *reinterpret_cast<const double2*>(sv + q * 64 + lane * 2);
+              m[q][0] = f.x; m[q][1] = f.y;
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < VW; ++e) {
+            const Vec4<T> x = ldv(vin + c[e]);
+            a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
+            a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
+            a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
+          }
+        } else {
+          for (int t = 0; t < ntail; ++t) {
+            const int cc = sc[t * 32 + lane];
+            T mm[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) mm[q] = sv[t * 288 + q * 32 + lane];
+            const Vec4<T> x = ldv(vin + cc);
+            a0 = fma(mm[0], x.x, fma(mm[1], x.y, fma(mm[2], x.z, a0)));
+            a1 = fma(mm[3], x.x, fma(mm[4], x.y, fma(mm[5], x.z, a1)));
+            a2 = fma(mm[6], x.x, fma(mm[7], x.y, fma(mm[8], x.z, a2)));
+          }
+        }
+        __syncwarp();
+        ++consumed;
+        if (tma_issue(P, pc, nw, lane, ring + (size_t)(issued % NST) * G::kStage, bars + issued % NST))
+          ++issued;
+      }
+      if (failed) break;
+      acc += finish_row<T, ADJ>(P, s * 32 + lane, a0, a1, a2, vin, vout, ch);
+    }
+    if (failed) {
+      // let this warp's own copies land (bounded) before the CTA exits
+      while (consumed < issued) {
+        const int sg = consumed % NST;
+        mbar_wait(bars + sg, (phase >> sg) & 1u);
+        phase ^= 1u << sg;
+        ++consumed;
+      }
+      atomicOr(ctl.err, 2);
+    }
+    if (__syncthreads_or(failed ? 1 : 0)) { st = ST_TIMEOUT; break; }
+    if (ctl.n_d > 0) {
+      if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+      for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
+        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+    }
+    acc = block_allreduce<NT>(acc, red);
+    double* part = ctl.partials + (l & 1) * gridDim.x;
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+    double s2 = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += part[q];
+    s2 = block_allreduce<NT>(s2, red);
+    theta = sqrt(s2) * ctl.norm_scale[0];
+    cur ^= 1;
+    if (!isfinite(theta)) { st = ST_NONFINITE; break; }
+    if (theta < ctl.theta_th) { st = ST_OK; break; }
+    if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+    th2 = th1;
+    th1 = theta;
+  }
+  if (st != ST_TIMEOUT && cur == 1) {
     for (int s = gw; s < P.n_slices; s += nw) {
       const int row = s * 32 + lane;
       stv(P.v0 + row, ldv(P.v1 + row));

@@ -94,6 +94,7 @@ struct vfpi_ctx {
   int nt = 0;      // threads per CTA
   int minb = 1;    // grid path: minimum CTAs per SM the kernel is compiled for
   int pf = 0;      // grid path: register prefetch of the next chunk
+  int tma_stages = 0;  // grid path: > 0 selects the TMA-staged kernel with this ring depth
   int max_grid = 0;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -185,8 +185,28 @@ static void* scenes_kernel(int nt, bool adj) {
   }
 }
 
+// TMA-staged grid kernels: (threads per CTA, stages per warp); dynamic shared memory.
 template <typename T>
-static void* pick_kernel(vfpi_ctx* c, bool adj) {
+static void* tma_kernel(int nt, int nst, bool adj, size_t* smem) {
+#define VFPI_TK(NT_, NS_)                                                               \
+  if (nt == NT_ && nst == NS_) {                                                        \
+    *smem = tma_smem_bytes<T, NT_, NS_>();                                              \
+    return adj ? (void*)&k_solve_grid_tma<T, NT_, NS_, true>                            \
+               : (void*)&k_solve_grid_tma<T, NT_, NS_, false>;                          \
+  }
+  VFPI_TK(256, 4) VFPI_TK(128, 4) VFPI_TK(128, 6) VFPI_TK(64, 8)
+#undef VFPI_TK
+  return nullptr;
+}
+
+template <typename T>
+static void* pick_kernel(vfpi_ctx* c, bool adj, size_t* smem) {
+  *smem = 0;
+  if (c->path == 1 && c->tma_stages > 0) {
+    // Barzilai-Borwein sweeps run on the register-staged kernel
+    if (!adj && c->bb_rule) return grid_kernel<T>(256, 2, 0, adj);
+    return tma_kernel<T>(c->nt, c->tma_stages, adj, smem);
+  }
   return c->path == 1 ? grid_kernel<T>(c->nt, c->minb, c->pf, adj) : scenes_kernel<T>(c->nt, adj);
 }
 
@@ -199,10 +219,14 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
     return e;
   int per_sm = 0;
   for (int adj = 0; adj < 2; ++adj) {  // one grid fits both modes
-    void* k = pick_kernel<T>(c, adj != 0);
+    size_t smem = 0;
+    void* k = pick_kernel<T>(c, adj != 0, &smem);
     if (!k) return cudaErrorInvalidValue;
+    if (smem > 0 &&
+        (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
     int q = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, 0)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, smem)) != cudaSuccess) return e;
     per_sm = adj ? std::min(per_sm, q) : q;
   }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -250,17 +274,19 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
   DevProblem<T> P = dev_problem<T>(c, adjoint);
   void* args[] = {&P, &ctl};
-  void* k = pick_kernel<T>(c, adjoint);
+  size_t smem = 0;
+  void* k = pick_kernel<T>(c, adjoint, &smem);
   if (!k) return cudaErrorInvalidValue;
   // inside a stream capture the events become graph nodes that record on replay
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
   const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
   if ((e = cudaEventRecordWithFlags(c->ev0, s, flags)) != cudaSuccess) return e;
+  const int nt = (c->path == 1 && c->tma_stages > 0 && !adjoint && c->bb_rule) ? 256 : c->nt;
   if (c->path == 1)
-    e = cudaLaunchCooperativeKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
+    e = cudaLaunchCooperativeKernel(k, dim3(c->grid), dim3(nt), args, smem, s);
   else
-    e = cudaLaunchKernel(k, dim3(c->grid), dim3(c->nt), args, 0, s);
+    e = cudaLaunchKernel(k, dim3(c->grid), dim3(nt), args, 0, s);
   if (e != cudaSuccess) return e;
   c->timed = true;
   return cudaEventRecordWithFlags(c->ev1, s, flags);

@@ -2,7 +2,8 @@
 
 For a solver already built on its problem, ``tune`` times candidate launch
 shapes -- for the grid-wide kernel: the kernel variant (threads per CTA, the
-CTAs-per-SM register budget, next-chunk prefetch) and the number of persistent
+CTAs-per-SM register budget, next-chunk prefetch, or shared-memory staging of
+the chunks by bulk copies with its ring depth) and the number of persistent
 CTAs (all that fit, the fewest that keep the same slices per warp, whole
 multiples of the SM count); for the CTA-per-scene kernel: the threads per CTA
 (warps working on one scene) -- each over a fixed number of sweeps of the
@@ -18,8 +19,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
-GRID_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7)
-WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8}
+GRID_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11)
+WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2}
 
 
 def _signature(solver, gpu: str) -> str:
