@@ -111,8 +111,9 @@ typedef struct {
   const int32_t* scene_ptr;/* [n_scenes+1] node offsets of the scenes (batched)     */
   int32_t block_threads;   /* 0 = default; threads per CTA of the solve kernel       */
   int32_t force_path;      /* 0 = auto, 1 = grid-wide kernel, 2 = CTA-per-scene      */
-  int32_t kernel_variant;  /* grid path: one of VFPI_VARIANT_* (threads per CTA,
-                              CTAs/SM register budget, prefetch); with 0 a nonzero
+  int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..11 (threads per
+                              CTA, CTAs/SM register budget, prefetch, TMA ring);
+                              scene path 0 or VFPI_VARIANT_CL_*; with 0 a nonzero
                               block_threads selects that CTA size, unbudgeted     */
   int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
                               fit, capped at one warp per 32-row slice)              */
@@ -140,7 +141,26 @@ enum {
   VFPI_VARIANT_TMA_256_4 = 8,
   VFPI_VARIANT_TMA_128_4 = 9,
   VFPI_VARIANT_TMA_128_6 = 10,
-  VFPI_VARIANT_TMA_64_8 = 11
+  VFPI_VARIANT_TMA_64_8 = 11,
+  /* Scene path (n_scenes > 1 or force_path 2): shared-memory-resident
+   * cluster kernel.  Each CTA copies its share of a scene's matrix into shared
+   * memory once per solve (1-D bulk copies) and every sweep reads it there; a
+   * scene larger than one CTA's share is split over the CTAs of a
+   * thread-block cluster, which meet at the cluster barrier once per sweep;
+   * smaller scenes go one per CTA.  Iterates are bitwise those of the
+   * CTA-per-scene kernel (variant 0).  Barzilai-Borwein solves run on the
+   * CTA-per-scene kernel.  Names: threads per CTA / CTAs per cluster / CTAs
+   * per SM (shared memory is split between them). */
+  VFPI_VARIANT_CL_256_1_1 = 16,
+  VFPI_VARIANT_CL_256_2_1 = 17,
+  VFPI_VARIANT_CL_256_4_1 = 18,
+  VFPI_VARIANT_CL_256_8_1 = 19,
+  VFPI_VARIANT_CL_128_4_2 = 20,
+  VFPI_VARIANT_CL_128_8_2 = 21,
+  VFPI_VARIANT_CL_256_4_2 = 22,
+  VFPI_VARIANT_CL_256_8_2 = 23,
+  VFPI_VARIANT_CL_512_8_1 = 24,
+  VFPI_VARIANT_CL_128_8_4 = 25
 };
 
 /* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,
@@ -221,8 +241,9 @@ vfpi_status vfpi_integrate(vfpi_t ctx, double* x_inout);
 vfpi_status vfpi_matvec(vfpi_t ctx, const void* x, void* y);
 
 /* Change the launch shape of the solve kernels after create (the tuner's
- * knob): kernel_variant and grid_ctas as in vfpi_opts (grid path),
- * block_threads for either path.  Synchronises. */
+ * knob): kernel_variant as in vfpi_opts (VFPI_ERR_INVALID_ARG for a variant
+ * the context's path does not have), grid_ctas (grid path), block_threads
+ * for either path.  Synchronises. */
 vfpi_status vfpi_configure_launch(vfpi_t ctx, int32_t kernel_variant, int32_t block_threads,
                                   int32_t grid_ctas);
 

@@ -125,7 +125,7 @@ void free_all(vfpi_ctx* c) {
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
-                  c->d_stage};
+                  c->d_stage, c->d_items};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -133,6 +133,52 @@ void free_all(vfpi_ctx* c) {
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// kernel_variant -> launch shape: grid path VFPI_VARIANT_DEFAULT..TMA_64_8;
+// scene path 0 (CTA-per-scene kernel, block_threads picks its size; the grid
+// variants 1..11 are ignored there) or one of the VFPI_VARIANT_CL_* cluster
+// shapes.  False for a variant the path does not have.
+bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
+  static const int grid_table[12][4] = {{256, 3, 0, 0}, {256, 4, 0, 0}, {512, 2, 0, 0}, {128, 8, 0, 0},
+                                        {256, 2, 1, 0}, {128, 4, 1, 0}, {512, 1, 1, 0}, {256, 2, 0, 0},
+                                        {256, 1, 0, 4}, {128, 1, 0, 4}, {128, 1, 0, 6}, {64, 1, 0, 8}};
+  // threads per CTA, CTAs per cluster, CTAs per SM
+  static const int cl_table[10][3] = {{256, 1, 1}, {256, 2, 1}, {256, 4, 1}, {256, 8, 1}, {128, 4, 2},
+                                      {128, 8, 2}, {256, 4, 2}, {256, 8, 2}, {512, 8, 1}, {128, 8, 4}};
+  const bool is_cl = v >= VFPI_VARIANT_CL_256_1_1 && v <= VFPI_VARIANT_CL_128_8_4;
+  if (v < 0 || (v > VFPI_VARIANT_TMA_64_8 && !is_cl)) return false;
+  if (c->path == 1 && is_cl) return false;
+  c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
+  c->minb = 1;
+  c->pf = 0;
+  c->tma_stages = 0;
+  c->cluster = 0;
+  c->cl_per_sm = 1;
+  if (c->path == 1 && (v > 0 || !block_threads)) {
+    c->nt = grid_table[v][0];
+    c->minb = grid_table[v][1];
+    c->pf = grid_table[v][2];
+    c->tma_stages = grid_table[v][3];
+  } else if (is_cl) {
+    const int* t = cl_table[v - VFPI_VARIANT_CL_256_1_1];
+    c->nt = t[0];
+    c->cluster = t[1];
+    c->cl_per_sm = t[2];
+  }
+  return true;
+}
+
+struct Shape {
+  int nt, minb, pf, tma_stages, cluster, cl_per_sm, grid_ctas;
+};
+Shape shape_of(const vfpi_ctx* c) {
+  return {c->nt, c->minb, c->pf, c->tma_stages, c->cluster, c->cl_per_sm, c->opts.grid_ctas};
+}
+void restore_shape(vfpi_ctx* c, const Shape& s) {
+  c->nt = s.nt; c->minb = s.minb; c->pf = s.pf; c->tma_stages = s.tma_stages;
+  c->cluster = s.cluster; c->cl_per_sm = s.cl_per_sm; c->opts.grid_ctas = s.grid_ctas;
+}
+
 
 // ---------------------------------------------------------------------------
 // dispatch helpers on dtype
@@ -613,24 +659,15 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   c->opts.grid_ctas = o->grid_ctas;
   if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
   if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
-  c->nt = o->block_threads ? o->block_threads : (c->path == 1 ? 256 : 128);
-  if (o->kernel_variant < 0 || o->kernel_variant > VFPI_VARIANT_TMA_64_8) {
-    c->err = "unknown kernel_variant";
+  if (!apply_variant(c, o->kernel_variant, o->block_threads)) {
+    c->err = "unknown kernel_variant for this path";
     return fail(VFPI_ERR_INVALID_ARG);
-  }
-  if (c->path == 1 && (o->kernel_variant > 0 || !o->block_threads)) {
-    static const int table[12][4] = {{256, 3, 0, 0}, {256, 4, 0, 0}, {512, 2, 0, 0}, {128, 8, 0, 0},
-                                     {256, 2, 1, 0}, {128, 4, 1, 0}, {512, 1, 1, 0}, {256, 2, 0, 0},
-                                     {256, 1, 0, 4}, {128, 1, 0, 4}, {128, 1, 0, 6}, {64, 1, 0, 8}};
-    c->nt = table[o->kernel_variant][0];
-    c->minb = table[o->kernel_variant][1];
-    c->pf = table[o->kernel_variant][2];
-    c->tma_stages = table[o->kernel_variant][3];
   }
   if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
   CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)std::max(c->max_grid, 1)));
+  CREATE_CUDA(dalloc(&c->d_items, 4 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(cudaStreamSynchronize(st));
   if (c->stage_bytes > (64u << 20)) {  // the copy of a host-side A is no longer needed
     cudaFree(c->d_stage);
@@ -891,42 +928,34 @@ vfpi_status vfpi_matvec(vfpi_t c, const void* x, void* y) {
 vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t block_threads,
                                   int32_t grid_ctas) {
   CTX_CHECK(c);
-  if (kernel_variant < 0 || kernel_variant > VFPI_VARIANT_TMA_64_8)
-    return arg_fail(c, VFPI_ERR_INVALID_ARG, "unknown kernel_variant");
   if (block_threads && block_threads != 64 && block_threads != 128 && block_threads != 256 &&
       block_threads != 512)
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
   if (grid_ctas < 0) return arg_fail(c, VFPI_ERR_INVALID_ARG, "grid_ctas must be >= 0");
   VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
-  const int nt0 = c->nt, mb0 = c->minb, pf0 = c->pf, tm0 = c->tma_stages, g0 = c->opts.grid_ctas;
-  c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
-  c->minb = 1;
-  c->pf = 0;
-  c->tma_stages = 0;
-  if (c->path == 1 && (kernel_variant > 0 || !block_threads)) {
-    static const int table[12][4] = {{256, 3, 0, 0}, {256, 4, 0, 0}, {512, 2, 0, 0}, {128, 8, 0, 0},
-                                     {256, 2, 1, 0}, {128, 4, 1, 0}, {512, 1, 1, 0}, {256, 2, 0, 0},
-                                     {256, 1, 0, 4}, {128, 1, 0, 4}, {128, 1, 0, 6}, {64, 1, 0, 8}};
-    c->nt = table[kernel_variant][0];
-    c->minb = table[kernel_variant][1];
-    c->pf = table[kernel_variant][2];
-    c->tma_stages = table[kernel_variant][3];
+  const Shape saved = shape_of(c);
+  if (!apply_variant(c, kernel_variant, block_threads)) {
+    restore_shape(c, saved);
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "unknown kernel_variant for this path");
   }
   c->opts.grid_ctas = grid_ctas;
   const int old_max = c->max_grid;
   cudaError_t e = DISPATCH(c, configure(c));
   if (e != cudaSuccess) {
-    c->nt = nt0; c->minb = mb0; c->pf = pf0; c->tma_stages = tm0; c->opts.grid_ctas = g0;
+    restore_shape(c, saved);
     DISPATCH(c, configure(c));
     return cuda_fail(c, e, "configure");
   }
   if (c->max_grid > old_max) {
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_bbpart) cudaFree(c->d_bbpart);
+    if (c->d_items) cudaFree(c->d_items);
     c->d_partials = nullptr;
     c->d_bbpart = nullptr;
+    c->d_items = nullptr;
     VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)c->max_grid));
     VFPI_TRY_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)c->max_grid));
+    VFPI_TRY_CUDA(dalloc(&c->d_items, 4 * (size_t)c->max_grid));
   }
   return VFPI_OK;
 }

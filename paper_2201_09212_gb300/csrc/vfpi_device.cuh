@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace vfpi {
@@ -97,6 +98,8 @@ struct SolveCtl {
   int32_t bb_rule;               // 0 off; W = alpha_l I with 1 bb1, 2 bb2, 3 alternating
   double bb_alpha0;              // alpha_1
   double* bb_part;               // [2][grid][3] FP64 partials of s.s, s.z, z.z (grid path)
+  int32_t* items;                // [grid] work item of each CTA (cluster path)
+  int32_t cache_entries;         // sliced-ELL entries one CTA holds in shared memory (cluster path)
 };
 
 // alpha_l from the three dot products (Sec. IV.C); the previous value stays
@@ -1155,6 +1158,261 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// batched solve with the scene matrices resident in shared memory
+// ---------------------------------------------------------------------------
+//
+// A scene's matrix is re-read by every sweep of Alg. 1 but is at most a few
+// MB; streaming it from HBM each sweep (k_solve_scenes) makes the batched
+// solve HBM-bound.  Here each CTA copies its share of a scene's sliced-ELL
+// entries into shared memory once per solve (1-D bulk copies completing on an
+// mbarrier) and every sweep reads them from there.  A scene too large for one
+// CTA is split over the CTAs of a thread-block cluster (contiguous slice
+// ranges), which meet at the hardware cluster barrier once per sweep (twice
+// with D-contacts) and add their FP64 residual partials in a fixed order, so
+// every CTA takes the same stop decision.  Smaller scenes go one per CTA.
+// The iterates are bitwise those of k_solve_scenes.
+
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_id_x() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// all threads of all CTAs of the cluster; release/acquire at cluster scope
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+// Block-row product of a slice held in shared memory (same layout and the
+// same operations in the same order as row_product).
+template <typename T>
+__device__ __forceinline__ void row_product_smem(const T* vb, const int32_t* cb, int len, int lane,
+                                                 const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  using I = typename std::conditional<sizeof(T) == 4, int4, int2>::type;
+  a0 = T(0); a1 = T(0); a2 = T(0);
+  const int nfull = len / VW;
+#pragma unroll 1
+  for (int k = 0; k < nfull; ++k) {
+    int c[VW];
+    T m[9][VW];
+    {
+      const I q = *reinterpret_cast<const I*>(cb + k * (32 * VW) + lane * VW);
+      const int* qp = reinterpret_cast<const int*>(&q);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) c[e] = qp[e];
+    }
+    const T* p = vb + k * (288 * VW) + lane * VW;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const V x = *reinterpret_cast<const V*>(p + q * (32 * VW));
+      const T* xp = reinterpret_cast<const T*>(&x);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) m[q][e] = xp[e];
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const Vec4<T> x = ldv(vin + c[e]);
+      a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
+      a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
+      a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
+    }
+  }
+  const int ntail = len - nfull * VW;
+  const T* pt = vb + nfull * (288 * VW) + lane;
+  const int32_t* ct = cb + nfull * (32 * VW) + lane;
+  for (int t = 0; t < ntail; ++t) {
+    const int c = ct[t * 32];
+    T m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) m[q] = pt[t * 288 + q * 32];
+    const Vec4<T> x = ldv(vin + c);
+    a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
+    a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
+    a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
+  }
+}
+
+// Sliced-ELL entries of slices [s0, s1) (slices are stored back to back).
+template <typename T>
+__device__ __forceinline__ int64_t slice_span(const DevProblem<T>& P, int s0, int s1) {
+  return s1 > s0 ? P.slice_off[s1 - 1] + P.slice_len[s1 - 1] - P.slice_off[s0] : 0;
+}
+
+constexpr int kClusterSmemHead = 128;   // mbarrier, padded to the copy alignment
+constexpr uint32_t kBulkPiece = 32768;  // bytes per bulk copy instruction
+
+template <typename T>
+constexpr int64_t cluster_entry_bytes() { return 288 * (int64_t)sizeof(T) + 128; }
+
+// One scene by a group of G CTAs (G = 1: this CTA alone; G = cluster size:
+// the whole cluster), this CTA being number g of the group.
+template <typename T, int NT, bool ADJ>
+__device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const SolveCtl& ctl, int sc,
+                                              int G, int g, double* slot, double* red,
+                                              unsigned char* dsm, uint32_t& phase, int& cache_ok) {
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
+  const int cap = ctl.cache_entries;
+  T* svals = reinterpret_cast<T*>(dsm + kClusterSmemHead);
+  int32_t* scols = reinterpret_cast<int32_t*>(dsm + kClusterSmemHead + (int64_t)cap * 288 * sizeof(T));
+  const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
+  const int ns = s1 - s0;
+  const int a = s0 + (int)((int64_t)g * ns / G);
+  const int b = s0 + (int)((int64_t)(g + 1) * ns / G);
+  // cached prefix [a, a + kc) of this CTA's slices
+  int kc = 0;
+  if (cache_ok)
+    while (a + kc < b && slice_span(P, a, a + kc + 1) <= cap) ++kc;
+  const int64_t e0 = b > a ? P.slice_off[a] : 0;
+  const int64_t ec = slice_span(P, a, a + kc);
+  if (ec > 0) {
+    if (threadIdx.x == 0) {
+      const uint32_t vbytes = (uint32_t)(ec * 288 * sizeof(T));
+      const uint32_t cbytes = (uint32_t)(ec * 128);
+      // the buffers were last read by ordinary loads of the previous scene
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(mbar, vbytes + cbytes);
+      const unsigned char* vsrc = reinterpret_cast<const unsigned char*>(P.vals + e0 * 288);
+      const unsigned char* csrc = reinterpret_cast<const unsigned char*>(P.cols + e0 * 32);
+      unsigned char* vdst = reinterpret_cast<unsigned char*>(svals);
+      unsigned char* cdst = reinterpret_cast<unsigned char*>(scols);
+      for (uint32_t o = 0; o < vbytes; o += kBulkPiece)
+        bulk_g2s(vdst + o, vsrc + o, vbytes - o < kBulkPiece ? vbytes - o : kBulkPiece, mbar);
+      for (uint32_t o = 0; o < cbytes; o += kBulkPiece)
+        bulk_g2s(cdst + o, csrc + o, cbytes - o < kBulkPiece ? cbytes - o : kBulkPiece, mbar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    if (ok) {
+      phase ^= 1u;
+    } else {  // copies did not land: stream this CTA's slices from HBM from now on
+      if (threadIdx.x == 0) atomicOr(ctl.err, 4);
+      cache_ok = 0;
+      kc = 0;
+    }
+  }
+  const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
+  const double nscale = ctl.norm_scale[sc];
+  int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  for (;; ++l) {
+    const Vec4<T>* vin = cur ? P.v1 : P.v0;
+    Vec4<T>* vout = cur ? P.v0 : P.v1;
+    ChebStep<T> ch;
+    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.accel = ch.on && l >= ctl.cheb_ls;
+    ch.nu = (T)nu;
+    ch.u = (T)ctl.cheb_u;
+    double acc = 0.0;
+    for (int s = a + wid; s < b; s += NT / 32) {
+      T a0, a1, a2;
+      if (s < a + kc) {
+        const int64_t lo = P.slice_off[s] - e0;
+        row_product_smem(svals + lo * 288, scols + lo * 32, P.slice_len[s], lane, vin, a0, a1, a2);
+      } else {
+        row_product(P, s, lane, vin, a0, a1, a2);
+      }
+      acc += finish_row<T, ADJ>(P, s * 32 + lane, a0, a1, a2, vin, vout, ch);
+    }
+    if (d1 > d0) {
+      if (G > 1) cluster_sync(); else __syncthreads();
+      for (int d = d0 + g * NT + threadIdx.x; d < d1; d += G * NT)
+        acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
+    }
+    double part = block_allreduce<NT>(acc, red);
+    if (G > 1) {
+      double* sl = slot + (l & 1) * G;
+      if (threadIdx.x == 0) sl[g] = part;
+      cluster_sync();
+      part = 0.0;
+      for (int k = 0; k < G; ++k) part += __ldcg(sl + k);
+    }
+    theta = sqrt(part) * nscale;
+    cur ^= 1;
+    if (!isfinite(theta)) { st = ST_NONFINITE; break; }
+    if (theta < ctl.theta_th) { st = ST_OK; break; }
+    if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+    th2 = th1;
+    th1 = theta;
+  }
+  if (cur == 1) {
+    for (int s = a + wid; s < b; s += NT / 32) {
+      const int row = s * 32 + lane;
+      stv(P.v0 + row, ldv(P.v1 + row));
+    }
+  }
+  if (g == 0 && threadIdx.x == 0) {
+    ctl.iters[sc] = l;
+    ctl.theta[sc] = theta;
+    ctl.status[sc] = st;
+  }
+}
+
+// Persistent clusters pop work items largest scene first: a scene that does
+// not fit one CTA's shared memory takes the whole cluster, otherwise each CTA
+// of the cluster takes a scene of its own.  Control flow that reaches a
+// cluster barrier depends only on values every CTA of the cluster reads alike.
+template <typename T, int NT, bool ADJ>
+__global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl ctl) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ double red[33];
+  const int C = (int)cluster_nctarank();
+  const int g = (int)cluster_ctarank();
+  const int cl = (int)cluster_id_x();
+  int32_t* item = ctl.items + (int64_t)cl * C;
+  double* slot = ctl.partials + (int64_t)cl * 2 * C;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int cache_ok = 1;
+  for (;;) {
+    if (g == 0 && threadIdx.x == 0) {
+      // item word: 2 * queue position + (1 if the whole cluster solves it)
+      const int q = atomicAdd(ctl.queue, 1);
+      int coop = 0;
+      if (q < ctl.n_scenes && C > 1) {
+        const int sc = ctl.order[q];
+        coop = slice_span(P, ctl.scene_slice[sc], ctl.scene_slice[sc + 1]) > ctl.cache_entries;
+      }
+      item[0] = 2 * q + coop;
+      if (C > 1) {
+        const int q2 = (q < ctl.n_scenes && !coop) ? atomicAdd(ctl.queue, C - 1) : ctl.n_scenes;
+        for (int k = 1; k < C; ++k) item[k] = coop ? 2 * q + 1 : 2 * (q2 + k - 1);
+      }
+    }
+    cluster_sync();
+    const int w0 = __ldcg(item);
+    if ((w0 >> 1) >= ctl.n_scenes) break;   // same word for every CTA of the cluster
+    const int w = __ldcg(item + g);
+    const int q = w >> 1;
+    if (w0 & 1) cluster_scene<T, NT, ADJ>(P, ctl, ctl.order[q], C, g, slot, red, dsm, phase, cache_ok);
+    else if (q < ctl.n_scenes)
+      cluster_scene<T, NT, ADJ>(P, ctl, ctl.order[q], 1, 0, slot, red, dsm, phase, cache_ok);
+    cluster_sync();   // the item words and residual slots are reused by the next item
+  }
+  // a copy that never landed must not outlive the CTA's shared memory
+  if (!cache_ok && threadIdx.x == 0) mbar_wait(mbar, phase);
 }
 
 // ---------------------------------------------------------------------------

@@ -95,6 +95,11 @@ struct vfpi_ctx {
   int minb = 1;    // grid path: minimum CTAs per SM the kernel is compiled for
   int pf = 0;      // grid path: register prefetch of the next chunk
   int tma_stages = 0;  // grid path: > 0 selects the TMA-staged kernel with this ring depth
+  int cluster = 0;     // scene path: > 0 selects the shared-memory-resident cluster kernel
+  int cl_per_sm = 1;   //   with this many CTAs per cluster and CTAs per SM
+  size_t dyn_smem = 0; //   shared memory per CTA and the sliced-ELL entries it holds
+  int cache_entries = 0;
+  int32_t* d_items = nullptr;  // [max_grid] per-CTA work items of the cluster kernel
   int max_grid = 0;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

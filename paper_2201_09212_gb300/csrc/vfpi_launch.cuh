@@ -200,8 +200,72 @@ static void* tma_kernel(int nt, int nst, bool adj, size_t* smem) {
 }
 
 template <typename T>
+static void* cluster_kernel(int nt, bool adj) {
+  switch (nt) {
+    case 128: return adj ? (void*)&k_solve_cluster<T, 128, true> : (void*)&k_solve_cluster<T, 128, false>;
+    case 256: return adj ? (void*)&k_solve_cluster<T, 256, true> : (void*)&k_solve_cluster<T, 256, false>;
+    case 512: return adj ? (void*)&k_solve_cluster<T, 512, true> : (void*)&k_solve_cluster<T, 512, false>;
+    default: return nullptr;
+  }
+}
+
+// Shared memory per CTA of the cluster kernel (the SM's capacity split over
+// cl_per_sm CTAs) and the sliced-ELL entries it holds; cluster occupancy.
+template <typename T>
+static cudaError_t configure_cluster(vfpi_ctx* c, int dev) {
+  int optin = 0, per_sm = 0, resv = 0;
+  cudaError_t e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+  void* ks[2] = {cluster_kernel<T>(c->nt, false), cluster_kernel<T>(c->nt, true)};
+  if (!ks[0] || !ks[1]) return cudaErrorInvalidValue;
+  size_t stat = 0;
+  for (void* k : ks) {
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return e;
+    stat = std::max(stat, fa.sharedSizeBytes);
+  }
+  const int64_t share = (int64_t)per_sm / c->cl_per_sm - resv - (int64_t)stat;
+  int64_t dyn = std::min<int64_t>(share, (int64_t)optin - (int64_t)stat);
+  dyn = dyn / 128 * 128;
+  if (dyn < kClusterSmemHead + cluster_entry_bytes<T>()) return cudaErrorInvalidConfiguration;
+  c->dyn_smem = (size_t)dyn;
+  c->cache_entries = (int)((dyn - kClusterSmemHead) / cluster_entry_bytes<T>());
+  int ncl = 0;
+  for (int a = 0; a < 2; ++a) {
+    if ((e = cudaFuncSetAttribute(ks[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
+      return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c->cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)c->cluster);
+    cfg.blockDim = dim3((unsigned)c->nt);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&n, ks[a], &cfg)) != cudaSuccess) return e;
+    ncl = a ? std::min(ncl, n) : n;
+  }
+  if (ncl < 1) return cudaErrorInvalidConfiguration;
+  c->max_grid = ncl * c->cluster;
+  c->grid = c->cluster * std::max(1, std::min(ncl, c->n_scenes));
+  return cudaSuccess;
+}
+
+template <typename T>
 static void* pick_kernel(vfpi_ctx* c, bool adj, size_t* smem) {
   *smem = 0;
+  if (c->path == 2 && c->cluster > 0) {
+    // Barzilai-Borwein sweeps run on the CTA-per-scene kernel
+    if (!adj && c->bb_rule) return scenes_kernel<T>(c->nt, adj);
+    *smem = c->dyn_smem;
+    return cluster_kernel<T>(c->nt, adj);
+  }
   if (c->path == 1 && c->tma_stages > 0) {
     // Barzilai-Borwein sweeps run on the register-staged kernel
     if (!adj && c->bb_rule) return grid_kernel<T>(256, 2, 0, adj);
@@ -217,6 +281,7 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
+  if (c->path == 2 && c->cluster > 0) return configure_cluster<T>(c, dev);
   int per_sm = 0;
   for (int adj = 0; adj < 2; ++adj) {  // one grid fits both modes
     size_t smem = 0;
@@ -268,6 +333,8 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.bb_rule = adjoint ? 0 : c->bb_rule;
   ctl.bb_alpha0 = c->bb_alpha0;
   ctl.bb_part = c->d_bbpart;
+  ctl.items = c->d_items;
+  ctl.cache_entries = c->cache_entries;
   // control words: barrier count/generation, error flag, scene queue
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -283,10 +350,26 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
   if ((e = cudaEventRecordWithFlags(c->ev0, s, flags)) != cudaSuccess) return e;
   const int nt = (c->path == 1 && c->tma_stages > 0 && !adjoint && c->bb_rule) ? 256 : c->nt;
-  if (c->path == 1)
+  const bool clustered = c->path == 2 && c->cluster > 0 && !(!adjoint && c->bb_rule);
+  if (c->path == 1) {
     e = cudaLaunchCooperativeKernel(k, dim3(c->grid), dim3(nt), args, smem, s);
-  else
-    e = cudaLaunchKernel(k, dim3(c->grid), dim3(nt), args, 0, s);
+  } else if (clustered) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c->cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)c->grid);
+    cfg.blockDim = dim3((unsigned)nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, k, args);
+  } else {
+    e = cudaLaunchKernel(k, dim3(std::max(1, std::min(c->grid, c->n_scenes))), dim3(nt), args, 0, s);
+  }
   if (e != cudaSuccess) return e;
   c->timed = true;
   return cudaEventRecordWithFlags(c->ev1, s, flags);

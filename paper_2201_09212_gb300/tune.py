@@ -5,9 +5,11 @@ shapes -- for the grid-wide kernel: the kernel variant (threads per CTA, the
 CTAs-per-SM register budget, next-chunk prefetch, or shared-memory staging of
 the chunks by bulk copies with its ring depth) and the number of persistent
 CTAs (all that fit, the fewest that keep the same slices per warp, whole
-multiples of the SM count); for the CTA-per-scene kernel: the threads per CTA
-(warps working on one scene) -- each over a fixed number of sweeps of the
-solver's own problem, timed with CUDA events, and keeps the fastest.  Results
+multiples of the SM count); for batched scenes: the threads per CTA of the
+CTA-per-scene kernel (warps working on one scene) and the shapes of the
+shared-memory-resident cluster kernel (threads per CTA, CTAs per cluster, CTAs
+per SM) -- each over a fixed number of sweeps of the solver's own problem,
+timed with CUDA events, and keeps the fastest.  Results
 are cached in a JSON file keyed by the layout signature and the GPU name, so a
 later solver of the same shape reuses them without timing.
 """
@@ -21,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
 GRID_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11)
 WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2}
+CLUSTER_VARIANTS = tuple(range(16, 26))
 
 
 def _signature(solver, gpu: str) -> str:
@@ -79,10 +82,14 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
                 trials.append(dict(kernel_variant=var, block_threads=0, grid_ctas=g,
                                    ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
     else:
-        for bt in (64, 128, 256):
-            solver.configure_launch(0, bt, 0)
+        shapes = [(0, bt) for bt in (64, 128, 256)] + [(v, 0) for v in CLUSTER_VARIANTS]
+        for var, bt in shapes:
+            try:
+                solver.configure_launch(var, bt, 0)
+            except RuntimeError:    # shape not available on this GPU
+                continue
             ms = _time(solver, sweeps, reps)
-            trials.append(dict(kernel_variant=0, block_threads=bt, grid_ctas=0,
+            trials.append(dict(kernel_variant=var, block_threads=bt, grid_ctas=0,
                                ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
     solver.set_tolerance(theta0, lmax0)
     best = min(trials, key=lambda t: t["ms_per_sweep"])
