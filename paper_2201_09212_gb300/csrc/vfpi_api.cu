@@ -118,7 +118,7 @@ cudaError_t out_view(vfpi_ctx* c, void* dst, size_t bytes, size_t slot, void** o
 }
 
 void free_all(vfpi_ctx* c) {
-  void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_vals, c->d_cols, c->d_b, c->d_w,
+  void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_slice_cmin, c->d_slice_cmax, c->d_vals, c->d_cols, c->d_b, c->d_w,
                   c->d_v0, c->d_v1, c->d_t0, c->d_t1, c->d_cslot, c->d_node_map, c->d_row_ptr, c->d_ds,
                   c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2,
                   c->d_lam, c->d_lam_star, c->d_dstar, c->d_scene_slice, c->d_scene_d, c->d_order,
@@ -559,6 +559,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   const size_t vec = c->esz * 4 * (size_t)c->n_pad;
   CREATE_CUDA(dalloc(&c->d_slice_len, 4 * (size_t)c->n_slices));
   CREATE_CUDA(dalloc(&c->d_slice_off, 8 * (size_t)c->n_slices));
+  CREATE_CUDA(dalloc(&c->d_slice_cmin, 4 * (size_t)std::max(c->n_slices, 1)));
+  CREATE_CUDA(dalloc(&c->d_slice_cmax, 4 * (size_t)std::max(c->n_slices, 1)));
   CREATE_CUDA(dalloc(&c->d_vals, c->esz * 288 * (size_t)c->n_entries));
   CREATE_CUDA(dalloc(&c->d_cols, 4 * 32 * (size_t)c->n_entries));
   CREATE_CUDA(dalloc(&c->d_b, vec));
@@ -667,7 +669,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_CUDA(DISPATCH(c, configure(c)));
   CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)std::max(c->max_grid, 1)));
-  CREATE_CUDA(dalloc(&c->d_items, 4 * (size_t)std::max(c->max_grid, 1)));
+  CREATE_CUDA(dalloc(&c->d_items, 8 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(cudaStreamSynchronize(st));
   if (c->stage_bytes > (64u << 20)) {  // the copy of a host-side A is no longer needed
     cudaFree(c->d_stage);
@@ -955,7 +957,7 @@ vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t bloc
     c->d_items = nullptr;
     VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)c->max_grid));
     VFPI_TRY_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)c->max_grid));
-    VFPI_TRY_CUDA(dalloc(&c->d_items, 4 * (size_t)c->max_grid));
+    VFPI_TRY_CUDA(dalloc(&c->d_items, 8 * (size_t)c->max_grid));
   }
   return VFPI_OK;
 }

@@ -51,6 +51,8 @@ struct DevProblem {
   const int64_t* slice_off;      // [n_slices] offset in entries (1 entry = 32 slots)
   const T* vals;                 // sliced-ELL values
   const int32_t* cols;           // sliced-ELL internal column indices
+  const int32_t* slice_cmin;     // [n_slices] smallest / largest column of a slice
+  const int32_t* slice_cmax;     //   (padding slots included)
   const Vec4<T>* b;              // [n_pad]
   const Vec4<T>* w;              // [n_pad]
   const int32_t* cslot;          // [n_pad] contact of the node or -1
@@ -98,8 +100,10 @@ struct SolveCtl {
   int32_t bb_rule;               // 0 off; W = alpha_l I with 1 bb1, 2 bb2, 3 alternating
   double bb_alpha0;              // alpha_1
   double* bb_part;               // [2][grid][3] FP64 partials of s.s, s.z, z.z (grid path)
-  int32_t* items;                // [grid] work item of each CTA (cluster path)
+  int32_t* items;                // [grid] work item of each CTA, then [grid / cluster] poison
+                                 //   words, zero at launch (cluster path)
   int32_t cache_entries;         // sliced-ELL entries one CTA holds in shared memory (cluster path)
+  int32_t smem_bytes;            // dynamic shared memory per CTA (cluster path)
 };
 
 // alpha_l from the three dot products (Sec. IV.C); the previous value stays
@@ -493,20 +497,19 @@ __device__ __forceinline__ double sqdiff(const Vec4<T>& a, const Vec4<T>& b) {
 // returns the row's contribution to ||dv||^2 (0 for a D-contact node, whose
 // update happens in phase 2).  ADJ selects the adjoint sweep (b is then dL/dv
 // and the contact step is the frozen linear map).
+// (vo, bb, ww, cs) = (v^l, b, W, contact slot) of the row, wherever they were read
+// from; out = where v^{l+1} of the row goes (holding v^{l-1}, which Chebyshev reads).
 template <typename T, bool ADJ>
-__device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T a0, T a1, T a2,
-                                             const Vec4<T>* vin, Vec4<T>* vout,
-                                             const ChebStep<T>& ch) {
-  const Vec4<T> vo = ldv(vin + row);
-  const Vec4<T> bb = ldv(P.b + row);
-  const Vec4<T> ww = ldv(P.w + row);
+__device__ __forceinline__ double finish_row_core(const DevProblem<T>& P, int row, T a0, T a1, T a2,
+                                                  const Vec4<T>& vo, const Vec4<T>& bb,
+                                                  const Vec4<T>& ww, int cs, Vec4<T>* out,
+                                                  const ChebStep<T>& ch) {
   // eq. (pgd1): v* = v - W (A v - b)
   Vec4<T> vn;
   vn.x = vo.x - ww.x * (a0 - bb.x);
   vn.y = vo.y - ww.y * (a1 - bb.y);
   vn.z = vo.z - ww.z * (a2 - bb.z);
   vn.w = T(0);
-  const int cs = __ldg(P.cslot + row);
   if (cs >= 0) {
     const int cj = __ldg(P.c_j + cs);
     if (cj >= 0) {  // D-contact: stage v* and finish in phase 2
@@ -539,9 +542,17 @@ __device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T 
       stv(P.lam_star + cs, ls);
     }
   }
-  if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, vout + row);
-  stv(vout + row, vn);
+  if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, out);   // *out holds v^{l-1}
+  stv(out, vn);
   return sqdiff(vn, vo);
+}
+
+template <typename T, bool ADJ>
+__device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T a0, T a1, T a2,
+                                             const Vec4<T>* vin, Vec4<T>* vout,
+                                             const ChebStep<T>& ch) {
+  return finish_row_core<T, ADJ>(P, row, a0, a1, a2, ldv(vin + row), ldv(P.b + row),
+                                 ldv(P.w + row), __ldg(P.cslot + row), vout + row, ch);
 }
 
 template <typename T, bool ADJ, bool PF = false>
@@ -1197,10 +1208,13 @@ __device__ __forceinline__ void cluster_sync() {
 }
 
 // Block-row product of a slice held in shared memory (same layout and the
-// same operations in the same order as row_product).
-template <typename T>
+// same operations in the same order as row_product).  VS: the gathered
+// iterate is the shared-memory copy vsrc[c - cmin] of v (else vsrc = v in
+// global memory, cmin = 0).
+template <typename T, bool VS>
 __device__ __forceinline__ void row_product_smem(const T* vb, const int32_t* cb, int len, int lane,
-                                                 const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+                                                 const Vec4<T>* vsrc, int cmin, T& a0, T& a1,
+                                                 T& a2) {
   constexpr int VW = Chunk<T>::VW;
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   using I = typename std::conditional<sizeof(T) == 4, int4, int2>::type;
@@ -1214,7 +1228,7 @@ __device__ __forceinline__ void row_product_smem(const T* vb, const int32_t* cb,
       const I q = *reinterpret_cast<const I*>(cb + k * (32 * VW) + lane * VW);
       const int* qp = reinterpret_cast<const int*>(&q);
 #pragma unroll
-      for (int e = 0; e < VW; ++e) c[e] = qp[e];
+      for (int e = 0; e < VW; ++e) c[e] = qp[e] - cmin;
     }
     const T* p = vb + k * (288 * VW) + lane * VW;
 #pragma unroll
@@ -1226,7 +1240,7 @@ __device__ __forceinline__ void row_product_smem(const T* vb, const int32_t* cb,
     }
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
-      const Vec4<T> x = ldv(vin + c[e]);
+      const Vec4<T> x = ldv(vsrc + c[e]);
       a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
       a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
       a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
@@ -1236,15 +1250,25 @@ __device__ __forceinline__ void row_product_smem(const T* vb, const int32_t* cb,
   const T* pt = vb + nfull * (288 * VW) + lane;
   const int32_t* ct = cb + nfull * (32 * VW) + lane;
   for (int t = 0; t < ntail; ++t) {
-    const int c = ct[t * 32];
+    const int c = ct[t * 32] - cmin;
     T m[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) m[q] = pt[t * 288 + q * 32];
-    const Vec4<T> x = ldv(vin + c);
+    const Vec4<T> x = ldv(vsrc + c);
     a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
     a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
     a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
   }
+}
+
+__device__ __forceinline__ Vec4<float> ldv_cg(const Vec4<float>* p) {
+  const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+  return {q.x, q.y, q.z, q.w};
+}
+__device__ __forceinline__ Vec4<double> ldv_cg(const Vec4<double>* p) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 c = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  return {a.x, a.y, c.x, c.y};
 }
 
 // Sliced-ELL entries of slices [s0, s1) (slices are stored back to back).
@@ -1253,62 +1277,104 @@ __device__ __forceinline__ int64_t slice_span(const DevProblem<T>& P, int s0, in
   return s1 > s0 ? P.slice_off[s1 - 1] + P.slice_len[s1 - 1] - P.slice_off[s0] : 0;
 }
 
-constexpr int kClusterSmemHead = 128;   // mbarrier, padded to the copy alignment
+// head of the cluster kernel's shared memory: the copy mbarrier [0], the two
+// iterate mbarriers [8, 16), residual slots [2][8] doubles [32, 160)
+constexpr int kClusterSmemHead = 256;
 constexpr uint32_t kBulkPiece = 32768;  // bytes per bulk copy instruction
 
 template <typename T>
-constexpr int64_t cluster_entry_bytes() { return 288 * (int64_t)sizeof(T) + 128; }
+__host__ __device__ constexpr int64_t cluster_entry_bytes() { return 288 * (int64_t)sizeof(T) + 128; }
+
+__host__ __device__ constexpr int64_t round128(int64_t x) { return (x + 127) / 128 * 128; }
+
+// Shared memory that staging the rows [r, r + nr) and the iterate's column
+// range of R rows takes (v, b, W as Vec4, contact slots as int).
+template <typename T>
+__host__ __device__ constexpr int64_t cluster_stage_bytes(int64_t R, int64_t nr) {
+  return round128(R * (int64_t)sizeof(Vec4<T>)) + 2 * round128(nr * (int64_t)sizeof(Vec4<T>)) +
+         round128(nr * 4);
+}
 
 // One scene by a group of G CTAs (G = 1: this CTA alone; G = cluster size:
-// the whole cluster), this CTA being number g of the group.
+// the whole cluster), this CTA being number g of the group.  Shared memory of
+// the CTA for the scene: [mbarrier | v over the CTA's column range | b, W and
+// contact slots of its rows | cached sliced-ELL values | their columns]; the
+// staging is left out when it would take more than half of it.
 template <typename T, int NT, bool ADJ>
 __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const SolveCtl& ctl, int sc,
                                               int G, int g, double* slot, double* red,
-                                              unsigned char* dsm, uint32_t& phase, int& cache_ok) {
+                                              unsigned char* dsm, uint32_t& phase, int& cache_ok,
+                                              int* poison) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
-  const int cap = ctl.cache_entries;
-  T* svals = reinterpret_cast<T*>(dsm + kClusterSmemHead);
-  int32_t* scols = reinterpret_cast<int32_t*>(dsm + kClusterSmemHead + (int64_t)cap * 288 * sizeof(T));
   const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
   const int ns = s1 - s0;
   const int a = s0 + (int)((int64_t)g * ns / G);
   const int b = s0 + (int)((int64_t)(g + 1) * ns / G);
+  const int row0 = a * 32, nr = (b - a) * 32;
+  // the range holds the CTA's own rows too (padding rows at a scene's end
+  // are nobody's column)
+  int cmin = row0, cmax = row0 + nr - 1;
+  for (int s = a; s < b; ++s) {
+    cmin = min(cmin, P.slice_cmin[s]);
+    cmax = max(cmax, P.slice_cmax[s]);
+  }
+  const int R = b > a ? cmax - cmin + 1 : 0;
+  const int64_t stage = cluster_stage_bytes<T>(R, nr);
+  const bool st = b > a && 2 * stage <= ctl.smem_bytes;
+  unsigned char* p = dsm + kClusterSmemHead;
+  Vec4<T>* vsm = reinterpret_cast<Vec4<T>*>(p);
+  Vec4<T>* bsm = reinterpret_cast<Vec4<T>*>(p + round128((int64_t)R * sizeof(Vec4<T>)));
+  Vec4<T>* wsm = bsm + round128((int64_t)nr * sizeof(Vec4<T>)) / sizeof(Vec4<T>);
+  int32_t* csm = reinterpret_cast<int32_t*>(wsm + round128((int64_t)nr * sizeof(Vec4<T>)) / sizeof(Vec4<T>));
+  if (st) p += stage;
+  T* svals = reinterpret_cast<T*>(p);
+  const int64_t cap = (ctl.smem_bytes - (p - dsm)) / cluster_entry_bytes<T>();
+  int32_t* scols = reinterpret_cast<int32_t*>(p + cap * 288 * (int64_t)sizeof(T));
   // cached prefix [a, a + kc) of this CTA's slices
   int kc = 0;
   if (cache_ok)
     while (a + kc < b && slice_span(P, a, a + kc + 1) <= cap) ++kc;
   const int64_t e0 = b > a ? P.slice_off[a] : 0;
   const int64_t ec = slice_span(P, a, a + kc);
-  if (ec > 0) {
-    if (threadIdx.x == 0) {
-      const uint32_t vbytes = (uint32_t)(ec * 288 * sizeof(T));
-      const uint32_t cbytes = (uint32_t)(ec * 128);
-      // the buffers were last read by ordinary loads of the previous scene
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(mbar, vbytes + cbytes);
-      const unsigned char* vsrc = reinterpret_cast<const unsigned char*>(P.vals + e0 * 288);
-      const unsigned char* csrc = reinterpret_cast<const unsigned char*>(P.cols + e0 * 32);
-      unsigned char* vdst = reinterpret_cast<unsigned char*>(svals);
-      unsigned char* cdst = reinterpret_cast<unsigned char*>(scols);
-      for (uint32_t o = 0; o < vbytes; o += kBulkPiece)
-        bulk_g2s(vdst + o, vsrc + o, vbytes - o < kBulkPiece ? vbytes - o : kBulkPiece, mbar);
-      for (uint32_t o = 0; o < cbytes; o += kBulkPiece)
-        bulk_g2s(cdst + o, csrc + o, cbytes - o < kBulkPiece ? cbytes - o : kBulkPiece, mbar);
+  if (ec > 0 && threadIdx.x == 0) {
+    const uint32_t vbytes = (uint32_t)(ec * 288 * sizeof(T));
+    const uint32_t cbytes = (uint32_t)(ec * 128);
+    // the buffers were last read by ordinary loads of the previous scene
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(mbar, vbytes + cbytes);
+    const unsigned char* vsrc = reinterpret_cast<const unsigned char*>(P.vals + e0 * 288);
+    const unsigned char* csrc = reinterpret_cast<const unsigned char*>(P.cols + e0 * 32);
+    unsigned char* vdst = reinterpret_cast<unsigned char*>(svals);
+    unsigned char* cdst = reinterpret_cast<unsigned char*>(scols);
+    for (uint32_t o = 0; o < vbytes; o += kBulkPiece)
+      bulk_g2s(vdst + o, vsrc + o, vbytes - o < kBulkPiece ? vbytes - o : kBulkPiece, mbar);
+    for (uint32_t o = 0; o < cbytes; o += kBulkPiece)
+      bulk_g2s(cdst + o, csrc + o, cbytes - o < kBulkPiece ? cbytes - o : kBulkPiece, mbar);
+  }
+  if (st)   // b, W (here dL/dv and W in the adjoint) and contact slots stay for the whole solve
+    for (int i = threadIdx.x; i < nr; i += NT) {
+      bsm[i] = ldv(P.b + row0 + i);
+      wsm[i] = ldv(P.w + row0 + i);
+      csm[i] = P.cslot[row0 + i];
     }
+  if (ec > 0) {
     const bool ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
     if (ok) {
       phase ^= 1u;
-    } else {  // copies did not land: stream this CTA's slices from HBM from now on
-      if (threadIdx.x == 0) atomicOr(ctl.err, 4);
+    } else {  // copies did not land: stream this CTA's slices, stop the cluster after this item
+      if (threadIdx.x == 0) {
+        atomicOr(ctl.err, 1 | 4);
+        *poison = 1;
+      }
       cache_ok = 0;
       kc = 0;
     }
   }
   const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
   const double nscale = ctl.norm_scale[sc];
-  int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+  int cur = 0, l = 1, status = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
@@ -1319,16 +1385,34 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
+    // v^l over this CTA's column range, read from L2 (other CTAs of the
+    // cluster wrote parts of it in the previous sweep)
+    if (st) {
+      for (int i = threadIdx.x; i < R; i += NT) vsm[i] = ldv_cg(vin + cmin + i);
+    }
+    __syncthreads();
     double acc = 0.0;
     for (int s = a + wid; s < b; s += NT / 32) {
       T a0, a1, a2;
       if (s < a + kc) {
         const int64_t lo = P.slice_off[s] - e0;
-        row_product_smem(svals + lo * 288, scols + lo * 32, P.slice_len[s], lane, vin, a0, a1, a2);
+        if (st)
+          row_product_smem<T, true>(svals + lo * 288, scols + lo * 32, P.slice_len[s], lane, vsm,
+                                    cmin, a0, a1, a2);
+        else
+          row_product_smem<T, false>(svals + lo * 288, scols + lo * 32, P.slice_len[s], lane, vin,
+                                     0, a0, a1, a2);
       } else {
         row_product(P, s, lane, vin, a0, a1, a2);
       }
-      acc += finish_row<T, ADJ>(P, s * 32 + lane, a0, a1, a2, vin, vout, ch);
+      const int row = s * 32 + lane;
+      if (st) {
+        const int i = row - row0;
+        acc += finish_row_core<T, ADJ>(P, row, a0, a1, a2, vsm[row - cmin], bsm[i], wsm[i], csm[i],
+                                       vout + row, ch);
+      } else {
+        acc += finish_row<T, ADJ>(P, row, a0, a1, a2, vin, vout, ch);
+      }
     }
     if (d1 > d0) {
       if (G > 1) cluster_sync(); else __syncthreads();
@@ -1345,9 +1429,9 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
     }
     theta = sqrt(part) * nscale;
     cur ^= 1;
-    if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < ctl.theta_th) { st = ST_OK; break; }
-    if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+    if (!isfinite(theta)) { status = ST_NONFINITE; break; }
+    if (theta < ctl.theta_th) { status = ST_OK; break; }
+    if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
     th1 = theta;
@@ -1361,30 +1445,253 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
   if (g == 0 && threadIdx.x == 0) {
     ctl.iters[sc] = l;
     ctl.theta[sc] = theta;
-    ctl.status[sc] = st;
+    ctl.status[sc] = status;
+  }
+}
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// Stores into another CTA's shared memory that count against that CTA's
+// mbarrier (complete_tx): the receiver sees the data once its phase completes.
+__device__ __forceinline__ void st_async_row(uint32_t dst, const Vec4<float>& v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
+      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void st_async_row(uint32_t dst, const Vec4<double>& v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(dst),
+               "d"(v.x), "d"(v.y), "r"(bar)
+               : "memory");
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+                   dst + 16),
+               "d"(v.z), "d"(v.w), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_f64(uint32_t dst, double x, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(dst),
+               "l"(__double_as_longlong(x)), "r"(bar)
+               : "memory");
+}
+
+// Work split of a scene over a group of G CTAs: member q gets slices
+// [a, b) and needs the iterate over columns [cmin, cmax] (its own rows
+// included).  tab[q] = {a, b, cmin, cmax}; fits: every member holds its
+// whole share -- both iterate buffers, staged rows and all its entries -- in
+// shared memory.  Computed by threads q < G, identically in every CTA.
+template <typename T>
+__device__ __forceinline__ int64_t dsm_bytes(const DevProblem<T>& P, const int* t) {
+  const int R = t[1] > t[0] ? t[3] - t[2] + 1 : 0;
+  const int64_t nr = 32 * (int64_t)(t[1] - t[0]);
+  return 2 * round128(R * (int64_t)sizeof(Vec4<T>)) + 2 * round128(nr * (int64_t)sizeof(Vec4<T>)) +
+         round128(nr * 4) + slice_span(P, t[0], t[1]) * cluster_entry_bytes<T>();
+}
+
+template <typename T>
+__device__ __forceinline__ void plan_scene(const DevProblem<T>& P, const SolveCtl& ctl, int sc, int G,
+                                           int (*tab)[4], int* fits) {
+  const int q = threadIdx.x;
+  if (q < G) {
+    const int s0 = ctl.scene_slice[sc], ns = ctl.scene_slice[sc + 1] - s0;
+    const int a = s0 + (int)((int64_t)q * ns / G), b = s0 + (int)((int64_t)(q + 1) * ns / G);
+    int cmin = a * 32, cmax = b * 32 - 1;
+    for (int s = a; s < b; ++s) {
+      cmin = min(cmin, P.slice_cmin[s]);
+      cmax = max(cmax, P.slice_cmax[s]);
+    }
+    tab[q][0] = a; tab[q][1] = b; tab[q][2] = cmin; tab[q][3] = cmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    for (int k = 0; k < G; ++k)
+      if (kClusterSmemHead + dsm_bytes(P, tab[k]) > ctl.smem_bytes) ok = 0;
+    *fits = ok;
+  }
+  __syncthreads();
+}
+
+// One scene held entirely in shared memory by a group of G CTAs (no
+// D-contacts).  The iterate lives in two buffers over each CTA's column
+// range; a CTA writes v^{l+1} of its rows into its own buffer and pushes each
+// row into every other member whose range covers it (st.async counting
+// against that member's iterate mbarrier), then sends its FP64 residual
+// partial the same way.  A member starts sweep l+1 once its mbarrier has seen
+// all rows and partials of sweep l; nothing goes through global memory but
+// lambda and the final v.
+template <typename T, int NT, bool ADJ>
+__device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const SolveCtl& ctl, int sc,
+                                                  int G, int g, const int (*tab)[4], double* red,
+                                                  unsigned char* dsm, uint32_t& phase,
+                                                  uint32_t& vphase, int& cache_ok, int* poison) {
+  constexpr int V4 = (int)sizeof(Vec4<T>);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
+  uint64_t* mbar_v = mbar + 1;
+  double* slots = reinterpret_cast<double*>(dsm + 32);
+  const int a = tab[g][0], b = tab[g][1], cmin = tab[g][2], cmax = tab[g][3];
+  const int row0 = a * 32, nr = (b - a) * 32;
+  const int R = b > a ? cmax - cmin + 1 : 0;
+  const int64_t vb = round128((int64_t)R * V4);
+  Vec4<T>* V0 = reinterpret_cast<Vec4<T>*>(dsm + kClusterSmemHead);
+  Vec4<T>* V1 = reinterpret_cast<Vec4<T>*>(dsm + kClusterSmemHead + vb);
+  Vec4<T>* bsm = reinterpret_cast<Vec4<T>*>(dsm + kClusterSmemHead + 2 * vb);
+  Vec4<T>* wsm = bsm + round128((int64_t)nr * V4) / V4;
+  int32_t* csm = reinterpret_cast<int32_t*>(wsm + round128((int64_t)nr * V4) / V4);
+  T* svals = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(csm) + round128((int64_t)nr * 4));
+  const int64_t ec = slice_span(P, a, b);   // all of the CTA's entries
+  int32_t* scols = reinterpret_cast<int32_t*>(svals + ec * 288);
+  const int64_t e0 = b > a ? P.slice_off[a] : 0;
+  if (ec > 0 && threadIdx.x == 0) {
+    const uint32_t vbytes = (uint32_t)(ec * 288 * sizeof(T));
+    const uint32_t cbytes = (uint32_t)(ec * 128);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(mbar, vbytes + cbytes);
+    const unsigned char* vsrc = reinterpret_cast<const unsigned char*>(P.vals + e0 * 288);
+    const unsigned char* csrc = reinterpret_cast<const unsigned char*>(P.cols + e0 * 32);
+    unsigned char* vdst = reinterpret_cast<unsigned char*>(svals);
+    unsigned char* cdst = reinterpret_cast<unsigned char*>(scols);
+    for (uint32_t o = 0; o < vbytes; o += kBulkPiece)
+      bulk_g2s(vdst + o, vsrc + o, vbytes - o < kBulkPiece ? vbytes - o : kBulkPiece, mbar);
+    for (uint32_t o = 0; o < cbytes; o += kBulkPiece)
+      bulk_g2s(cdst + o, csrc + o, cbytes - o < kBulkPiece ? cbytes - o : kBulkPiece, mbar);
+  }
+  for (int i = threadIdx.x; i < nr; i += NT) {
+    bsm[i] = ldv(P.b + row0 + i);
+    wsm[i] = ldv(P.w + row0 + i);
+    csm[i] = P.cslot[row0 + i];
+  }
+  for (int i = threadIdx.x; i < R; i += NT) V0[i] = ldv(P.v0 + cmin + i);   // warm start v^1
+  // bytes this CTA receives per sweep: the rows of the other members inside
+  // its column range, and their partials
+  int64_t expect = 8 * (int64_t)(G - 1);
+  for (int q = 0; q < G; ++q)
+    if (q != g) {
+      const int lo = max(tab[q][0] * 32, cmin), hi = min(tab[q][1] * 32 - 1, cmax);
+      if (hi >= lo) expect += (int64_t)(hi - lo + 1) * V4;
+    }
+  const uint32_t base = smem_u32(dsm);
+  bool ok = true;
+  if (ec > 0) ok = mbar_wait(mbar, phase);
+  if (!__syncthreads_and(ok ? 1 : 0)) {   // the matrix did not arrive: give the scene up
+    if (threadIdx.x == 0) {
+      atomicOr(ctl.err, 1);
+      ctl.status[sc] = ST_TIMEOUT;
+      *poison = 1;
+    }
+    cache_ok = 0;
+    return;
+  }
+  if (ec > 0) phase ^= 1u;
+  const double nscale = ctl.norm_scale[sc];
+  int l = 1, status = ST_NOT_CONVERGED, fin = 0;
+  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  for (;; ++l) {
+    const int pb = (l - 1) & 1, nb = pb ^ 1;
+    const Vec4<T>* Vp = pb ? V1 : V0;
+    Vec4<T>* Vn = pb ? V0 : V1;
+    if (G > 1 && threadIdx.x == 0) mbar_arrive_expect_tx(mbar_v + nb, (uint32_t)expect);
+    ChebStep<T> ch;
+    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.accel = ch.on && l >= ctl.cheb_ls;
+    ch.nu = (T)nu;
+    ch.u = (T)ctl.cheb_u;
+    double acc = 0.0;
+    for (int s = a + wid; s < b; s += NT / 32) {
+      T a0, a1, a2;
+      const int64_t lo = P.slice_off[s] - e0;
+      row_product_smem<T, true>(svals + lo * 288, scols + lo * 32, P.slice_len[s], lane, Vp, cmin, a0,
+                                a1, a2);
+      const int row = s * 32 + lane;
+      const int i = row - row0;
+      Vec4<T>* out = Vn + (row - cmin);
+      acc += finish_row_core<T, ADJ>(P, row, a0, a1, a2, Vp[row - cmin], bsm[i], wsm[i], csm[i], out, ch);
+      if (G > 1) {
+        const Vec4<T> vn = ldv(out);
+        for (int q = 0; q < G; ++q) {
+          if (q == g || row < tab[q][2] || row > tab[q][3]) continue;
+          const int64_t vbq = round128((int64_t)(tab[q][3] - tab[q][2] + 1) * V4);
+          const uint32_t off = (uint32_t)(kClusterSmemHead + nb * vbq + (int64_t)(row - tab[q][2]) * V4);
+          st_async_row(mapa_u32(base + off, q), vn, mapa_u32(smem_u32(mbar_v + nb), q));
+        }
+      }
+    }
+    double part = block_allreduce<NT>(acc, red);
+    if (G > 1) {
+      if (threadIdx.x == 0) {
+        slots[nb * 8 + g] = part;
+        for (int q = 0; q < G; ++q)
+          if (q != g)
+            st_async_f64(mapa_u32(smem_u32(slots + nb * 8 + g), q), part,
+                         mapa_u32(smem_u32(mbar_v + nb), q));
+      }
+      const bool got = mbar_wait(mbar_v + nb, (vphase >> nb) & 1u);
+      if (!__syncthreads_and(got ? 1 : 0)) {
+        if (threadIdx.x == 0) {
+          atomicOr(ctl.err, 1);
+          *poison = 1;
+        }
+        status = ST_TIMEOUT;
+        fin = nb;
+        break;
+      }
+      vphase ^= 1u << nb;
+      part = 0.0;
+      for (int k = 0; k < G; ++k) part += slots[nb * 8 + k];
+    }
+    theta = sqrt(part) * nscale;
+    fin = nb;
+    if (!isfinite(theta)) { status = ST_NONFINITE; break; }
+    if (theta < ctl.theta_th) { status = ST_OK; break; }
+    if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
+    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+    th2 = th1;
+    th1 = theta;
+  }
+  const Vec4<T>* Vf = fin ? V1 : V0;
+  for (int i = threadIdx.x; i < nr; i += NT) stv(P.v0 + row0 + i, Vf[row0 + i - cmin]);
+  if (g == 0 && threadIdx.x == 0) {
+    ctl.iters[sc] = l;
+    ctl.theta[sc] = theta;
+    ctl.status[sc] = status;
   }
 }
 
 // Persistent clusters pop work items largest scene first: a scene that does
 // not fit one CTA's shared memory takes the whole cluster, otherwise each CTA
-// of the cluster takes a scene of its own.  Control flow that reaches a
-// cluster barrier depends only on values every CTA of the cluster reads alike.
+// of the cluster takes a scene of its own.  A scene runs from shared memory
+// alone (cluster_scene_dsm) when every member holds its whole share and it
+// has no D-contacts, else through L2 (cluster_scene).  Control flow that
+// reaches a cluster barrier depends only on values every CTA of the cluster
+// reads alike; a member whose bounded wait ran out marks the cluster's poison
+// word, and the whole cluster stops at the next item.
 template <typename T, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl ctl) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ double red[33];
+  __shared__ int tab[8][4];
+  __shared__ int fits;
   const int C = (int)cluster_nctarank();
   const int g = (int)cluster_ctarank();
   const int cl = (int)cluster_id_x();
+  const int n_cl = (int)(gridDim.x / C);
   int32_t* item = ctl.items + (int64_t)cl * C;
+  int32_t* poison = ctl.items + (int64_t)n_cl * C + cl;
   double* slot = ctl.partials + (int64_t)cl * 2 * C;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    mbar_init(mbar + 2, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t phase = 0, vphase = 0;
   int cache_ok = 1;
   for (;;) {
     if (g == 0 && threadIdx.x == 0) {
@@ -1393,7 +1700,10 @@ __global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl 
       int coop = 0;
       if (q < ctl.n_scenes && C > 1) {
         const int sc = ctl.order[q];
-        coop = slice_span(P, ctl.scene_slice[sc], ctl.scene_slice[sc + 1]) > ctl.cache_entries;
+        const int sa = ctl.scene_slice[sc], sb = ctl.scene_slice[sc + 1];
+        const int64_t rows = 32 * (int64_t)(sb - sa);
+        const int64_t room = ctl.smem_bytes - kClusterSmemHead - cluster_stage_bytes<T>(rows, rows);
+        coop = slice_span(P, sa, sb) * cluster_entry_bytes<T>() > room;
       }
       item[0] = 2 * q + coop;
       if (C > 1) {
@@ -1401,15 +1711,24 @@ __global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl 
         for (int k = 1; k < C; ++k) item[k] = coop ? 2 * q + 1 : 2 * (q2 + k - 1);
       }
     }
-    cluster_sync();
+    cluster_sync();   // (also: every CTA of the cluster has started and set up its mbarriers)
     const int w0 = __ldcg(item);
-    if ((w0 >> 1) >= ctl.n_scenes) break;   // same word for every CTA of the cluster
+    if ((w0 >> 1) >= ctl.n_scenes || __ldcg(poison)) break;   // same words for the whole cluster
     const int w = __ldcg(item + g);
     const int q = w >> 1;
-    if (w0 & 1) cluster_scene<T, NT, ADJ>(P, ctl, ctl.order[q], C, g, slot, red, dsm, phase, cache_ok);
-    else if (q < ctl.n_scenes)
-      cluster_scene<T, NT, ADJ>(P, ctl, ctl.order[q], 1, 0, slot, red, dsm, phase, cache_ok);
-    cluster_sync();   // the item words and residual slots are reused by the next item
+    const int G = (w0 & 1) ? C : 1;
+    if (G > 1 || q < ctl.n_scenes) {
+      const int sc = ctl.order[q];
+      plan_scene(P, ctl, sc, G, tab, &fits);
+      const bool no_d = ctl.scene_d[sc + 1] == ctl.scene_d[sc];
+      if (fits && no_d && cache_ok)
+        cluster_scene_dsm<T, NT, ADJ>(P, ctl, sc, G, G > 1 ? g : 0, tab, red, dsm, phase, vphase,
+                                      cache_ok, poison);
+      else
+        cluster_scene<T, NT, ADJ>(P, ctl, sc, G, G > 1 ? g : 0, slot, red, dsm, phase, cache_ok,
+                                  poison);
+    }
+    cluster_sync();   // the item words, residual slots and iterate buffers are reused next
   }
   // a copy that never landed must not outlive the CTA's shared memory
   if (!cache_ok && threadIdx.x == 0) mbar_wait(mbar, phase);
@@ -1446,6 +1765,33 @@ __global__ void k_check_finite(const T* __restrict__ a, int64_t n, int* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     if (!isfinite(a[i])) atomicOr(err, 8);
+}
+
+// Smallest and largest column of each slice (one warp per slice).
+static __global__ void k_slice_colrange(int n_slices, const int32_t* __restrict__ slice_len,
+                                        const int64_t* __restrict__ slice_off,
+                                        const int32_t* __restrict__ cols, int32_t* __restrict__ cmin,
+                                        int32_t* __restrict__ cmax) {
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= n_slices) return;
+  const int64_t base = slice_off[s] * 32;
+  const int n = slice_len[s] * 32;
+  int lo = 0x7fffffff, hi = -1;
+  for (int k = lane; k < n; k += 32) {
+    const int c = cols[base + k];
+    lo = min(lo, c);
+    hi = max(hi, c);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (lane == 0) {
+    cmin[s] = n > 0 ? lo : s * 32;
+    cmax[s] = n > 0 ? hi : s * 32;
+  }
 }
 
 // Fill every slot with a zero block pointing at its own row.

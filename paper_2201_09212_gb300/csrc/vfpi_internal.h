@@ -56,6 +56,7 @@ struct vfpi_ctx {
   // device memory (owned)
   int32_t *d_slice_len = nullptr;
   int64_t* d_slice_off = nullptr;
+  int32_t *d_slice_cmin = nullptr, *d_slice_cmax = nullptr;  // column range of each slice
   void* d_vals = nullptr;
   int32_t* d_cols = nullptr;
   void *d_b = nullptr, *d_w = nullptr, *d_v0 = nullptr, *d_v1 = nullptr;
@@ -99,7 +100,7 @@ struct vfpi_ctx {
   int cl_per_sm = 1;   //   with this many CTAs per cluster and CTAs per SM
   size_t dyn_smem = 0; //   shared memory per CTA and the sliced-ELL entries it holds
   int cache_entries = 0;
-  int32_t* d_items = nullptr;  // [max_grid] per-CTA work items of the cluster kernel
+  int32_t* d_items = nullptr;  // [2 max_grid] work items and poison words of the cluster kernel
   int max_grid = 0;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -19,6 +19,8 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.slice_off = c->d_slice_off;
   P.vals = static_cast<const T*>(c->d_vals);
   P.cols = c->d_cols;
+  P.slice_cmin = c->d_slice_cmin;
+  P.slice_cmax = c->d_slice_cmax;
   P.b = static_cast<const Vec4<T>*>(c->d_b);
   P.w = static_cast<const Vec4<T>*>(c->d_w);
   P.cslot = c->d_cslot;
@@ -84,6 +86,10 @@ cudaError_t Launch<T>::build_layout(vfpi_ctx* c, const int32_t* row_ptr, const i
     k_scatter_blocks<T><<<blocks_for(c->N, 128), 128, 0, s>>>(
         c->N, row_ptr, col_idx, static_cast<const T*>(vals), c->d_node_map, c->d_slice_len,
         c->d_slice_off, c->d_cols, static_cast<T*>(c->d_vals), store_cols ? 1 : 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (store_cols && c->n_slices > 0)
+    k_slice_colrange<<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
+        c->n_slices, c->d_slice_len, c->d_slice_off, c->d_cols, c->d_slice_cmin, c->d_slice_cmax);
   return cudaGetLastError();
 }
 
@@ -335,10 +341,14 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.bb_part = c->d_bbpart;
   ctl.items = c->d_items;
   ctl.cache_entries = c->cache_entries;
+  ctl.smem_bytes = (int32_t)c->dyn_smem;
   // control words: barrier count/generation, error flag, scene queue
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  if (c->path == 2 && c->cluster > 0 &&
+      (e = cudaMemsetAsync(c->d_items, 0, 8 * (size_t)c->max_grid, s)) != cudaSuccess)
+    return e;
   DevProblem<T> P = dev_problem<T>(c, adjoint);
   void* args[] = {&P, &ctl};
   size_t smem = 0;
