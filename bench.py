@@ -50,12 +50,18 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes_per_sweep(sc, esz=4) -> int:
+def algorithmic_bytes_per_sweep(sc, esz=4, sym=False) -> int:
     """Bytes one sweep must move at minimum: every block and column index once,
     the row pointers, v^l read, b read, v^{l+1} written, W read, the contact
-    records (R, mu, phi, node ids: 48 B) and lambda written (12 B)."""
+    records (R, mu, phi, node ids: 48 B) and lambda written (12 B).  With the
+    symmetric storage (A = A^T) only the (nnzb + N) / 2 blocks c >= r carry
+    values and a column; the (nnzb - N) / 2 blocks c < r cost their column
+    alone (their values are the transposes read again)."""
     N, n, nnzb, n_c = sc.n_nodes, sc.n, sc.nnzb, sc.n_c
-    return (nnzb * (9 * esz + 4) + 4 * (N + 1) + 3 * esz * n + esz * N + n_c * (48 + 12))
+    vec = 4 * (N + 1) + 3 * esz * n + esz * N + n_c * (48 + 12)
+    if sym:
+        return ((nnzb + N) // 2) * (9 * esz + 4) + ((nnzb - N) // 2) * 4 + vec
+    return nnzb * (9 * esz + 4) + vec
 
 
 def peaks():
@@ -274,13 +280,16 @@ def batched_bench(args, torch, dev, stream, rank):
     per_scene_total = float(np.mean(per_ms)) / 1e3 * S
     first_batch = kms[0] / 1e3
     threads = s.layout()["threads"]
+    var = int(tuned.get("kernel_variant", 0))
+    kname = (f"k_solve_cluster<float,{threads}> (launch shape {var})" if var >= 16
+             else f"k_solve_scenes<float,{threads}>")
     s.close()
     return {
         "workload": f"{S} lattices, side U{{4..12}}, {int(nq.sum()) * 3} DOF, {sc.nnzb} blocks, {sc.n_c} contacts",
         "env_steps_per_s": env_sps, "ms_per_env_step": 1e3 * t_total / args.batch_steps,
         "steps": args.batch_steps, "dof_iters_per_s": dof_iters / t_total,
         "iters_per_scene": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
-        "solve_kernel": {"name": f"k_solve_scenes<float,{threads}>", "ms_avg": 1e3 * k_avg,
+        "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
                          "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0]},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
         "per_scene_plain": {"sample": len(sample), "mean_solve_ms": float(np.mean(per_ms)),
@@ -446,7 +455,8 @@ def main():
             dist.destroy_process_group()
         return
 
-    bps = algorithmic_bytes_per_sweep(sc)
+    sym = 12 <= int(tuned["kernel_variant"]) <= 15
+    bps = algorithmic_bytes_per_sweep(sc, sym=sym)
     k_avg = float(np.mean(kms)) / 1e3
     it_avg = float(np.mean(iters))
     achieved = bps * it_avg / k_avg / 1e9
@@ -455,7 +465,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": (tr * it_avg if tr else None),
-                "algorithmic_bytes_per_sweep": bps, "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}",
+                "algorithmic_bytes_per_sweep": bps,
+                "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
+                          + (" (symmetric storage)" if sym else ""),
                 "kernel_ms_avg": 1e3 * k_avg}
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -473,7 +485,9 @@ def main():
                    "launch": {"kernel_variant": tuned["kernel_variant"], "ctas": lay["grid"],
                               "threads": lay["threads"], "tuned_ms_per_sweep": tuned["ms_per_sweep"],
                               "from_cache": tuned["cached"]},
-                   "l2": "inputs larger than L2 (549 MB of blocks streamed per sweep)"},
+                   "l2": ("inputs larger than L2 (" + (
+                       f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks"
+                       if sym else f"{sc.nnzb * 40 / 1e6:.0f} MB of blocks") + " streamed per sweep)")},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

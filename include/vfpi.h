@@ -142,6 +142,17 @@ enum {
   VFPI_VARIANT_TMA_128_4 = 9,
   VFPI_VARIANT_TMA_128_6 = 10,
   VFPI_VARIANT_TMA_64_8 = 11,
+  /* Symmetric storage (grid path; needs A = A^T exactly, which create and
+   * update check): only the blocks with c >= r are stored in the sliced-ELL
+   * layout, and each row's blocks c < r are read back transposed from
+   * there (through L2), about 40 % fewer bytes from HBM per sweep.  The
+   * entries are summed in the same order, so the iterates are bitwise those
+   * of the full storage; if an update makes A unsymmetric the same shape runs
+   * on the full storage.  Threads per CTA / CTAs per SM register budget. */
+  VFPI_VARIANT_SYM_256_2 = 12,
+  VFPI_VARIANT_SYM_256_3 = 13,
+  VFPI_VARIANT_SYM_256_4 = 14,
+  VFPI_VARIANT_SYM_512_1 = 15,
   /* Scene path (n_scenes > 1 or force_path 2): shared-memory-resident
    * cluster kernel.  Each CTA copies its share of a scene's matrix into shared
    * memory once per solve (1-D bulk copies) and every sweep reads it there; a

@@ -125,7 +125,8 @@ void free_all(vfpi_ctx* c) {
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
-                  c->d_stage, c->d_items};
+                  c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
+                  c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -145,16 +146,25 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
   // threads per CTA, CTAs per cluster, CTAs per SM
   static const int cl_table[10][3] = {{256, 1, 1}, {256, 2, 1}, {256, 4, 1}, {256, 8, 1}, {128, 4, 2},
                                       {128, 8, 2}, {256, 4, 2}, {256, 8, 2}, {512, 8, 1}, {128, 8, 4}};
+  // symmetric storage: threads per CTA, CTAs/SM register budget
+  static const int sym_table[4][2] = {{256, 2}, {256, 3}, {256, 4}, {512, 1}};
   const bool is_cl = v >= VFPI_VARIANT_CL_256_1_1 && v <= VFPI_VARIANT_CL_128_8_4;
-  if (v < 0 || (v > VFPI_VARIANT_TMA_64_8 && !is_cl)) return false;
+  const bool is_sym = v >= VFPI_VARIANT_SYM_256_2 && v <= VFPI_VARIANT_SYM_512_1;
+  if (v < 0 || (v > VFPI_VARIANT_SYM_512_1 && !is_cl)) return false;
   if (c->path == 1 && is_cl) return false;
+  if (is_sym && (c->path != 1 || !c->sym_ok)) return false;
   c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
   c->minb = 1;
   c->pf = 0;
   c->tma_stages = 0;
   c->cluster = 0;
   c->cl_per_sm = 1;
-  if (c->path == 1 && (v > 0 || !block_threads)) {
+  c->sym = 0;
+  if (is_sym) {
+    c->nt = sym_table[v - VFPI_VARIANT_SYM_256_2][0];
+    c->minb = sym_table[v - VFPI_VARIANT_SYM_256_2][1];
+    c->sym = 1;
+  } else if (c->path == 1 && (v > 0 || !block_threads)) {
     c->nt = grid_table[v][0];
     c->minb = grid_table[v][1];
     c->pf = grid_table[v][2];
@@ -169,14 +179,15 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
 }
 
 struct Shape {
-  int nt, minb, pf, tma_stages, cluster, cl_per_sm, grid_ctas;
+  int nt, minb, pf, tma_stages, cluster, cl_per_sm, grid_ctas, sym;
 };
 Shape shape_of(const vfpi_ctx* c) {
-  return {c->nt, c->minb, c->pf, c->tma_stages, c->cluster, c->cl_per_sm, c->opts.grid_ctas};
+  return {c->nt, c->minb, c->pf, c->tma_stages, c->cluster, c->cl_per_sm, c->opts.grid_ctas, c->sym};
 }
 void restore_shape(vfpi_ctx* c, const Shape& s) {
   c->nt = s.nt; c->minb = s.minb; c->pf = s.pf; c->tma_stages = s.tma_stages;
   c->cluster = s.cluster; c->cl_per_sm = s.cl_per_sm; c->opts.grid_ctas = s.grid_ctas;
+  c->sym = s.sym;
 }
 
 
@@ -368,6 +379,73 @@ vfpi_status read_err(vfpi_ctx* c, int* flags) {
   return VFPI_OK;
 }
 
+// Symmetric storage of A (grid path): on the first call (with the staged
+// pattern dcol) size and lay out the upper and lower structures; every call
+// checks A = A^T bitwise and scatters the upper values.  A matrix that is not
+// symmetric, or too large for the 31-bit positions, just leaves sym_ok = 0
+// (the solve then reads the full storage, with the same iterates).
+vfpi_status set_sym(vfpi_ctx* c, const int32_t* dcol, const void* dv, bool first) {
+  if (first) {
+    c->sym_ok = 0;
+    const int N = c->N;
+    VFPI_TRY_CUDA(dalloc(&c->d_col_idx, 4 * (size_t)std::max(c->nnzb, 1)));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_col_idx, dcol, 4 * (size_t)c->nnzb, cudaMemcpyDeviceToDevice, c->stream));
+    VFPI_TRY_CUDA(dalloc(&c->d_nlow, 4 * (size_t)std::max(N, 1)));
+    VFPI_TRY_CUDA(DISPATCH(c, sym_nlow(c, c->d_row_ptr, c->d_col_idx)));
+    std::vector<int32_t> nlow(N), rp(N + 1);
+    VFPI_TRY_CUDA(cudaMemcpyAsync(nlow.data(), c->d_nlow, 4 * (size_t)N, cudaMemcpyDeviceToHost, c->stream));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(rp.data(), c->d_row_ptr, 4 * ((size_t)N + 1), cudaMemcpyDeviceToHost, c->stream));
+    VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> ulen(c->n_slices, 0), llen(c->n_slices, 0);
+    for (int i = 0; i < N; ++i) {
+      const int s = c->h_node_map[i] / 32;
+      ulen[s] = std::max(ulen[s], rp[i + 1] - rp[i] - nlow[i]);
+      llen[s] = std::max(llen[s], nlow[i]);
+    }
+    std::vector<int64_t> uoff(c->n_slices), loff(c->n_slices);
+    int64_t nu = 0, nl = 0;
+    for (int s = 0; s < c->n_slices; ++s) {
+      uoff[s] = nu;
+      loff[s] = nl;
+      nu += ulen[s];
+      nl += llen[s];
+    }
+    if ((nu + 1) * 288 >= (int64_t(1) << 30)) return VFPI_OK;   // positions would not fit
+    c->n_uent = nu;
+    c->n_lent = nl;
+    VFPI_TRY_CUDA(dalloc(&c->d_ulen, 4 * (size_t)std::max(c->n_slices, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_llen, 4 * (size_t)std::max(c->n_slices, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_uoff, 8 * (size_t)std::max(c->n_slices, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_loff, 8 * (size_t)std::max(c->n_slices, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_uvals, c->esz * 288 * (size_t)(nu + 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_ucols, 4 * 32 * (size_t)std::max<int64_t>(nu, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_lcols, 4 * 32 * (size_t)std::max<int64_t>(nl, 1)));
+    VFPI_TRY_CUDA(dalloc(&c->d_lpos, 4 * 32 * (size_t)std::max<int64_t>(nl, 1)));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_ulen, ulen.data(), 4 * (size_t)c->n_slices, cudaMemcpyHostToDevice, c->stream));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_llen, llen.data(), 4 * (size_t)c->n_slices, cudaMemcpyHostToDevice, c->stream));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_uoff, uoff.data(), 8 * (size_t)c->n_slices, cudaMemcpyHostToDevice, c->stream));
+    VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_loff, loff.data(), 8 * (size_t)c->n_slices, cudaMemcpyHostToDevice, c->stream));
+    VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    VFPI_TRY_CUDA(DISPATCH(c, sym_pattern(c)));
+    int flags = 0;
+    vfpi_status st = read_err(c, &flags);
+    if (st != VFPI_OK) return st;
+    if (flags) {   // pattern not symmetric: no symmetric storage for this context
+      cudaFree(c->d_uvals);
+      c->d_uvals = nullptr;
+      return VFPI_OK;
+    }
+  }
+  if (!c->d_uvals) return VFPI_OK;
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  VFPI_TRY_CUDA(DISPATCH(c, sym_values(c, dv, first)));
+  int flags = 0;
+  vfpi_status st = read_err(c, &flags);
+  if (st != VFPI_OK) return st;
+  c->sym_ok = flags ? 0 : 1;
+  return VFPI_OK;
+}
+
 // A's values: checked finite, then scattered into the sliced-ELL layout.  With
 // store_cols the pattern (drow, dcol: device copies) is laid out too; without
 // it only the values are replaced and the stored pattern is reused.
@@ -383,6 +461,7 @@ vfpi_status set_values(vfpi_ctx* c, const int32_t* drow, const int32_t* dcol, co
   if (st != VFPI_OK) return st;
   if (flags) return arg_fail(c, VFPI_ERR_NONFINITE, "A has non-finite values");
   VFPI_TRY_CUDA(DISPATCH(c, build_layout(c, drow, dcol, dv, store_cols)));
+  if (c->path == 1) return set_sym(c, dcol, dv, store_cols);
   return VFPI_OK;
 }
 
@@ -640,6 +719,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
       return fail(VFPI_ERR_INVALID_ARG);
     }
   }
+  c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
   CREATE_ST(set_values(c, drow, dcol, A->vals, true, off_vals));
   // contacts, b, W
   CREATE_ST(set_contacts(c, Jc));

@@ -77,6 +77,19 @@ struct DevProblem {
   Vec4<T>* v1;
   Vec4<T>* r0;                   // Barzilai-Borwein: residuals A v^l - b of the
   Vec4<T>* r1;                   //   current and previous sweep (ping-pong)
+  // Symmetric storage (grid path, A = A^T exactly): the blocks with c >= r in
+  // the same sliced-ELL layout, plus for each row its entries c < r as
+  // (column, 2 * position of component 0 of block (c, r) in uvals + 1 if that
+  // block sits in a slice's leftover part, where components are 32 apart
+  // instead of 32 VW); padding points at a zero block after the last entry.
+  const T* uvals;
+  const int32_t* ucols;
+  const int32_t* uslice_len;
+  const int64_t* uslice_off;
+  const int32_t* lcols;
+  const int32_t* lpos;
+  const int32_t* lslice_len;
+  const int64_t* lslice_off;
 };
 
 struct SolveCtl {
@@ -326,6 +339,94 @@ __device__ __forceinline__ void row_product_prefetch(const DevProblem<T>& P, int
   }
 }
 
+// Block-row product from the symmetric storage: the row's entries c < r are
+// the transposes of blocks (c, r) stored with row c, read back through L2
+// (their first reader brought them from HBM); then its entries c >= r.  The
+// entries are summed in the same order (ascending column) with the same
+// operations as row_product, so the result is bitwise the same.
+template <typename T>
+__device__ __forceinline__ void lower_entry(const DevProblem<T>& P, int c, int pos, const Vec4<T>* vin,
+                                            T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  const T* b = P.uvals + (pos >> 1);
+  const int st = (pos & 1) ? 32 : 32 * VW;
+  T m[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) m[q] = __ldcg(b + q * st);
+  const Vec4<T> x = ldv(vin + c);
+  // (A_rc)_ij = (A_cr)_ji
+  a0 = fma(m[0], x.x, fma(m[3], x.y, fma(m[6], x.z, a0)));
+  a1 = fma(m[1], x.x, fma(m[4], x.y, fma(m[7], x.z, a1)));
+  a2 = fma(m[2], x.x, fma(m[5], x.y, fma(m[8], x.z, a2)));
+}
+
+template <typename T>
+__device__ __forceinline__ void row_product_sym(const DevProblem<T>& P, int slice, int lane,
+                                                const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  a0 = T(0); a1 = T(0); a2 = T(0);
+  {
+    const int len = P.lslice_len[slice];
+    const int64_t off = P.lslice_off[slice];
+    const int32_t* __restrict__ cb = P.lcols + off * 32;
+    const int32_t* __restrict__ pb = P.lpos + off * 32;
+    const int nfull = len / VW;
+#pragma unroll 1
+    for (int k = 0; k < nfull; ++k) {
+      int c[VW], q[VW];
+      Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
+      Chunk<T>::cols(pb + (int64_t)k * (32 * VW) + lane * VW, q);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) lower_entry(P, c[e], q[e], vin, a0, a1, a2);
+    }
+    const int ntail = len - nfull * VW;
+    for (int t = 0; t < ntail; ++t) {
+      const int64_t o = (int64_t)nfull * (32 * VW) + t * 32 + lane;
+      lower_entry(P, __ldcs(cb + o), __ldcs(pb + o), vin, a0, a1, a2);
+    }
+  }
+  const int len = P.uslice_len[slice];
+  const int64_t off = P.uslice_off[slice];
+  const T* __restrict__ vb = P.uvals + off * 288;
+  const int32_t* __restrict__ cb = P.ucols + off * 32;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int nfull = len / VW;
+#pragma unroll 1
+  for (int k = 0; k < nfull; ++k) {
+    int c[VW];
+    T m[9][VW];
+    Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
+    const T* p = vb + (int64_t)k * (288 * VW) + lane * VW;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {   // kept in L2 for the rows below that read them transposed
+      const V x = __ldcg(reinterpret_cast<const V*>(p + q * (32 * VW)));
+      const T* xp = reinterpret_cast<const T*>(&x);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) m[q][e] = xp[e];
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const Vec4<T> x = ldv(vin + c[e]);
+      a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
+      a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
+      a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
+    }
+  }
+  const int ntail = len - nfull * VW;
+  const T* pt = vb + (int64_t)nfull * (288 * VW) + lane;
+  const int32_t* ct = cb + (int64_t)nfull * (32 * VW) + lane;
+  for (int t = 0; t < ntail; ++t) {
+    const int c = __ldcs(ct + t * 32);
+    T m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) m[q] = __ldcg(pt + t * 288 + q * 32);
+    const Vec4<T> x = ldv(vin + c);
+    a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
+    a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
+    a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one-shot contact solve (Alg. 2, strict operator of eq. operator)
 // ---------------------------------------------------------------------------
@@ -555,12 +656,13 @@ __device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T 
                                  ldv(P.w + row), __ldg(P.cslot + row), vout + row, ch);
 }
 
-template <typename T, bool ADJ, bool PF = false>
+template <typename T, bool ADJ, bool PF = false, bool SYM = false>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
                                             const Vec4<T>* vin, Vec4<T>* vout,
                                             const ChebStep<T>& ch) {
   T a0, a1, a2;
-  if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
+  if constexpr (SYM) row_product_sym(P, slice, lane, vin, a0, a1, a2);
+  else if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
   else row_product(P, slice, lane, vin, a0, a1, a2);
   return finish_row<T, ADJ>(P, slice * 32 + lane, a0, a1, a2, vin, vout, ch);
 }
@@ -747,7 +849,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
 // gw, gw + W, ...; one barrier per sweep (two with D-contacts).  theta is the
 // fixed-order sum of the per-CTA partials, computed identically by every CTA,
 // so all CTAs take the same stop decision without a further exchange.
-template <typename T, int NT, int MINB, bool PF, bool ADJ>
+template <typename T, int NT, int MINB, bool PF, bool ADJ, bool SYM = false>
 __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[33];
   __shared__ int s_ok;
@@ -805,7 +907,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
           acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
       }
     } else {
-      for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF>(P, s, lane, vin, vout, ch);
+      for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF, SYM>(P, s, lane, vin, vout, ch);
       if (ctl.n_d > 0) {
         if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
@@ -1831,6 +1933,121 @@ __global__ void k_scatter_blocks(int N, const int32_t* __restrict__ row_ptr,
     const T* src = vals + (int64_t)(r0 + e) * 9;
 #pragma unroll
     for (int q = 0; q < 9; ++q) svals[vp + (int64_t)q * vs] = src[q];
+  }
+}
+
+// ---- symmetric storage set-up (caller's sorted BSR pattern, one scene) ----
+
+// Index of the diagonal block in each row = the row's number of entries c < r.
+static __global__ void k_row_nlow(int N, const int32_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col_idx, int32_t* __restrict__ nlow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int lo = row_ptr[i], hi = row_ptr[i + 1];
+  while (lo < hi) {   // first entry with column >= i
+    const int mid = (lo + hi) >> 1;
+    if (col_idx[mid] < i) lo = mid + 1; else hi = mid;
+  }
+  nlow[i] = lo - row_ptr[i];
+}
+
+__device__ __forceinline__ int find_col(const int32_t* __restrict__ row_ptr,
+                                        const int32_t* __restrict__ col_idx, int row, int col) {
+  int lo = row_ptr[row], hi = row_ptr[row + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = col_idx[mid];
+    if (c == col) return mid;
+    if (c < col) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Error bit 32: the pattern is not symmetric; 64: a block differs from the
+// transpose of its mirror (bitwise).
+template <typename T>
+__global__ void k_sym_check(int N, const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col_idx, const T* __restrict__ vals, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    const int c = col_idx[e];
+    const int f = find_col(row_ptr, col_idx, c, i);
+    if (f < 0) { atomicOr(err, 32); return; }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (!(vals[(int64_t)e * 9 + 3 * a + b] == vals[(int64_t)f * 9 + 3 * b + a])) {
+          atomicOr(err, 64);
+          return;
+        }
+  }
+}
+
+// Padding of both structures: upper slots point at the slice's first row
+// (their values stay zero); lower slots at that row and the zero block.
+template <typename T>
+__global__ void k_fill_sym_pad(int n_slices, const int32_t* __restrict__ ulen,
+                               const int64_t* __restrict__ uoff, int32_t* __restrict__ ucols,
+                               const int32_t* __restrict__ llen, const int64_t* __restrict__ loff,
+                               int32_t* __restrict__ lcols, int32_t* __restrict__ lpos, int64_t zero) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_slices * 32) return;
+  const int s = row >> 5, lane = row & 31;
+  for (int k = lane; k < ulen[s] * 32; k += 32) ucols[uoff[s] * 32 + k] = s * 32;
+  for (int k = lane; k < llen[s] * 32; k += 32) {
+    lcols[loff[s] * 32 + k] = s * 32;
+    lpos[loff[s] * 32 + k] = (int32_t)(((zero + (k & 31)) << 1) | 1);
+  }
+}
+
+// Blocks with c >= r into the upper structure (values; columns too when
+// store_cols).
+template <typename T>
+__global__ void k_scatter_upper(int N, const int32_t* __restrict__ row_ptr,
+                                const int32_t* __restrict__ col_idx, const T* __restrict__ vals,
+                                const int32_t* __restrict__ nlow, const int32_t* __restrict__ node_map,
+                                const int32_t* __restrict__ ulen, const int64_t* __restrict__ uoff,
+                                int32_t* __restrict__ ucols, T* __restrict__ uvals, int store_cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int p = node_map[i];
+  const int s = p >> 5, lane = p & 31;
+  const int r0 = row_ptr[i] + nlow[i], r1 = row_ptr[i + 1];
+  for (int e = 0; e < r1 - r0; ++e) {
+    int64_t vp;
+    int vs;
+    const int64_t cp = slot_pos<T>(uoff[s], ulen[s], e, lane, &vp, &vs);
+    if (store_cols) ucols[cp] = node_map[col_idx[r0 + e]];
+    const T* src = vals + (int64_t)(r0 + e) * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) uvals[vp + (int64_t)q * vs] = src[q];
+  }
+}
+
+// Entries c < r: the column and where block (c, r) sits in the upper values.
+template <typename T>
+__global__ void k_build_lower(int N, const int32_t* __restrict__ row_ptr,
+                              const int32_t* __restrict__ col_idx, const int32_t* __restrict__ nlow,
+                              const int32_t* __restrict__ node_map, const int32_t* __restrict__ ulen,
+                              const int64_t* __restrict__ uoff, const int32_t* __restrict__ llen,
+                              const int64_t* __restrict__ loff, int32_t* __restrict__ lcols,
+                              int32_t* __restrict__ lpos, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int p = node_map[i];
+  const int s = p >> 5, lane = p & 31;
+  for (int j = 0; j < nlow[i]; ++j) {
+    const int c = col_idx[row_ptr[i] + j];
+    const int f = find_col(row_ptr, col_idx, c, i);
+    if (f < 0) { atomicOr(err, 32); return; }
+    const int u = f - row_ptr[c] - nlow[c];   // i > c: among row c's entries >= c
+    const int pc = node_map[c];
+    int64_t vp, vp2;
+    int vs, vs2;
+    slot_pos<T>(uoff[pc >> 5], ulen[pc >> 5], u, pc & 31, &vp, &vs);
+    const int64_t cp = slot_pos<T>(loff[s], llen[s], j, lane, &vp2, &vs2);
+    lcols[cp] = pc;
+    lpos[cp] = (int32_t)((vp << 1) | (vs == 32 ? 1 : 0));
   }
 }
 

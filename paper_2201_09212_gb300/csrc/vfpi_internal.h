@@ -31,6 +31,11 @@ struct Launch {
   static cudaError_t spmv(vfpi_ctx* c, const void* x_int, void* y_int);
   static cudaError_t solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoint);
   static cudaError_t configure(vfpi_ctx* c);
+  // symmetric storage: diagonal index of each row; padding and the lower
+  // entries' positions; symmetry check (error bits 32/64) and upper values
+  static cudaError_t sym_nlow(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx);
+  static cudaError_t sym_pattern(vfpi_ctx* c);
+  static cudaError_t sym_values(vfpi_ctx* c, const void* vals, bool store_cols);
 };
 
 }  // namespace vfpi
@@ -57,6 +62,14 @@ struct vfpi_ctx {
   int32_t *d_slice_len = nullptr;
   int64_t* d_slice_off = nullptr;
   int32_t *d_slice_cmin = nullptr, *d_slice_cmax = nullptr;  // column range of each slice
+  // symmetric storage (grid path, built when A = A^T exactly)
+  int sym_ok = 0;                           // built and A currently symmetric
+  int64_t n_uent = 0, n_lent = 0;           // entries (32 slots each) of the two structures
+  int32_t *d_col_idx = nullptr, *d_nlow = nullptr;
+  int32_t *d_ulen = nullptr, *d_llen = nullptr;
+  int64_t *d_uoff = nullptr, *d_loff = nullptr;
+  void* d_uvals = nullptr;
+  int32_t *d_ucols = nullptr, *d_lcols = nullptr, *d_lpos = nullptr;
   void* d_vals = nullptr;
   int32_t* d_cols = nullptr;
   void *d_b = nullptr, *d_w = nullptr, *d_v0 = nullptr, *d_v1 = nullptr;
@@ -96,6 +109,7 @@ struct vfpi_ctx {
   int minb = 1;    // grid path: minimum CTAs per SM the kernel is compiled for
   int pf = 0;      // grid path: register prefetch of the next chunk
   int tma_stages = 0;  // grid path: > 0 selects the TMA-staged kernel with this ring depth
+  int sym = 0;         // grid path: product from the symmetric storage (when sym_ok)
   int cluster = 0;     // scene path: > 0 selects the shared-memory-resident cluster kernel
   int cl_per_sm = 1;   //   with this many CTAs per cluster and CTAs per SM
   size_t dyn_smem = 0; //   shared memory per CTA and the sliced-ELL entries it holds

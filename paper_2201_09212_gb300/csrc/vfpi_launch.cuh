@@ -21,6 +21,14 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.cols = c->d_cols;
   P.slice_cmin = c->d_slice_cmin;
   P.slice_cmax = c->d_slice_cmax;
+  P.uvals = static_cast<const T*>(c->d_uvals);
+  P.ucols = c->d_ucols;
+  P.uslice_len = c->d_ulen;
+  P.uslice_off = c->d_uoff;
+  P.lcols = c->d_lcols;
+  P.lpos = c->d_lpos;
+  P.lslice_len = c->d_llen;
+  P.lslice_off = c->d_loff;
   P.b = static_cast<const Vec4<T>*>(c->d_b);
   P.w = static_cast<const Vec4<T>*>(c->d_w);
   P.cslot = c->d_cslot;
@@ -180,6 +188,55 @@ static void* grid_kernel(int nt, int minb, int pf, bool adj) {
   return nullptr;
 }
 
+// Grid-path kernels on the symmetric storage.
+template <typename T>
+static void* grid_kernel_sym(int nt, int minb, bool adj) {
+#define VFPI_GS(NT_, MB_)                                                               \
+  if (nt == NT_ && minb == MB_)                                                         \
+    return adj ? (void*)&k_solve_grid<T, NT_, MB_, false, true, true>                   \
+               : (void*)&k_solve_grid<T, NT_, MB_, false, false, true>;
+  VFPI_GS(256, 2) VFPI_GS(256, 3) VFPI_GS(256, 4) VFPI_GS(512, 1)
+#undef VFPI_GS
+  return nullptr;
+}
+
+template <typename T>
+cudaError_t Launch<T>::sym_nlow(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx) {
+  if (c->N > 0) k_row_nlow<<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->N, row_ptr, col_idx, c->d_nlow);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::sym_pattern(vfpi_ctx* c) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_uvals, 0, (size_t)(c->n_uent + 1) * 288 * sizeof(T), s)) != cudaSuccess)
+    return e;
+  if (c->n_slices > 0)
+    k_fill_sym_pad<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
+        c->n_slices, c->d_ulen, c->d_uoff, c->d_ucols, c->d_llen, c->d_loff, c->d_lcols, c->d_lpos,
+        c->n_uent * 288);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (c->N > 0)
+    k_build_lower<T><<<blocks_for(c->N, 128), 128, 0, s>>>(
+        c->N, c->d_row_ptr, c->d_col_idx, c->d_nlow, c->d_node_map, c->d_ulen, c->d_uoff, c->d_llen,
+        c->d_loff, c->d_lcols, c->d_lpos, c->d_err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::sym_values(vfpi_ctx* c, const void* vals, bool store_cols) {
+  cudaStream_t s = c->stream;
+  if (c->N > 0) {
+    k_sym_check<T><<<blocks_for(c->N, 128), 128, 0, s>>>(c->N, c->d_row_ptr, c->d_col_idx,
+                                                         static_cast<const T*>(vals), c->d_err);
+    k_scatter_upper<T><<<blocks_for(c->N, 128), 128, 0, s>>>(
+        c->N, c->d_row_ptr, c->d_col_idx, static_cast<const T*>(vals), c->d_nlow, c->d_node_map,
+        c->d_ulen, c->d_uoff, c->d_ucols, static_cast<T*>(c->d_uvals), store_cols ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 static void* scenes_kernel(int nt, bool adj) {
   switch (nt) {
@@ -277,6 +334,8 @@ static void* pick_kernel(vfpi_ctx* c, bool adj, size_t* smem) {
     if (!adj && c->bb_rule) return grid_kernel<T>(256, 2, 0, adj);
     return tma_kernel<T>(c->nt, c->tma_stages, adj, smem);
   }
+  if (c->path == 1 && c->sym && c->sym_ok && !(!adj && c->bb_rule))
+    return grid_kernel_sym<T>(c->nt, c->minb, adj);
   return c->path == 1 ? grid_kernel<T>(c->nt, c->minb, c->pf, adj) : scenes_kernel<T>(c->nt, adj);
 }
 
@@ -298,6 +357,13 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
       return e;
     int q = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, smem)) != cudaSuccess) return e;
+    if (c->path == 1 && c->sym) {   // falls back to the full storage if A stops being symmetric
+      int q2 = 0;
+      void* kf = grid_kernel<T>(c->nt, c->minb, 0, adj != 0);
+      if (!kf) return cudaErrorInvalidValue;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q2, kf, c->nt, 0)) != cudaSuccess) return e;
+      q = std::min(q, q2);
+    }
     per_sm = adj ? std::min(per_sm, q) : q;
   }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;

@@ -2,8 +2,9 @@
 
 For a solver already built on its problem, ``tune`` times candidate launch
 shapes -- for the grid-wide kernel: the kernel variant (threads per CTA, the
-CTAs-per-SM register budget, next-chunk prefetch, or shared-memory staging of
-the chunks by bulk copies with its ring depth) and the number of persistent
+CTAs-per-SM register budget, next-chunk prefetch, shared-memory staging of
+the chunks by bulk copies with its ring depth, or the symmetric storage of A)
+and the number of persistent
 CTAs (all that fit, the fewest that keep the same slices per warp, whole
 multiples of the SM count); for batched scenes: the threads per CTA of the
 CTA-per-scene kernel (warps working on one scene) and the shapes of the
@@ -21,8 +22,9 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
-GRID_VARIANTS = (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11)
-WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2}
+GRID_VARIANTS = tuple(range(16))      # 12..15 need an exactly symmetric A
+WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2,
+         12: 8, 13: 8, 14: 8, 15: 16}
 CLUSTER_VARIANTS = tuple(range(16, 26))
 
 
@@ -74,7 +76,10 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
     trials = []
     if lay["path"] == 1:
         for var in GRID_VARIANTS:
-            solver.configure_launch(var, 0, 0)
+            try:
+                solver.configure_launch(var, 0, 0)
+            except RuntimeError:    # symmetric storage needs A = A^T
+                continue
             l2 = solver.layout()
             for g in _grid_candidates(l2["n_slices"], WARPS[var], l2["max_grid"], l2["sms"]):
                 solver.configure_launch(var, 0, g)

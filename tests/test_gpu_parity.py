@@ -354,7 +354,7 @@ def test_every_launch_variant_gives_identical_iterates():
     sc = scenes.terrain_lattice(dims=(40, 36, 6))
     ref = None
     with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=12, force_path=1) as s:
-        for var in range(12):
+        for var in range(16):   # 12..15: symmetric storage
             for grid in (0, 17):
                 s.configure_launch(var, 0, grid)
                 r = s.solve(sc.v0)
