@@ -382,7 +382,7 @@ vfpi_status read_err(vfpi_ctx* c, int* flags) {
 // Symmetric storage of A (grid path): on the first call (with the staged
 // pattern dcol) size and lay out the upper and lower structures; every call
 // checks A = A^T bitwise and scatters the upper values.  A matrix that is not
-// symmetric, or too large for the 31-bit positions, just leaves sym_ok = 0
+// symmetric, or too large for 31-bit positions, just leaves sym_ok = 0
 // (the solve then reads the full storage, with the same iterates).
 vfpi_status set_sym(vfpi_ctx* c, const int32_t* dcol, const void* dv, bool first) {
   if (first) {
@@ -410,7 +410,7 @@ vfpi_status set_sym(vfpi_ctx* c, const int32_t* dcol, const void* dv, bool first
       nu += ulen[s];
       nl += llen[s];
     }
-    if ((nu + 1) * 288 >= (int64_t(1) << 30)) return VFPI_OK;   // positions would not fit
+    if ((nu + 1) * 288 >= (int64_t(1) << 31)) return VFPI_OK;   // positions would not fit
     c->n_uent = nu;
     c->n_lent = nl;
     VFPI_TRY_CUDA(dalloc(&c->d_ulen, 4 * (size_t)std::max(c->n_slices, 1)));

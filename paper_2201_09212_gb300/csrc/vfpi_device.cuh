@@ -77,11 +77,12 @@ struct DevProblem {
   Vec4<T>* v1;
   Vec4<T>* r0;                   // Barzilai-Borwein: residuals A v^l - b of the
   Vec4<T>* r1;                   //   current and previous sweep (ping-pong)
-  // Symmetric storage (grid path, A = A^T exactly): the blocks with c >= r in
-  // the same sliced-ELL layout, plus for each row its entries c < r as
-  // (column, 2 * position of component 0 of block (c, r) in uvals + 1 if that
-  // block sits in a slice's leftover part, where components are 32 apart
-  // instead of 32 VW); padding points at a zero block after the last entry.
+  // Symmetric storage (grid path, A = A^T exactly): the blocks with c >= r,
+  // sliced like the full storage but each entry lane-contiguous (values
+  // [9][32], columns [32]), plus for each row its entries c < r as (column,
+  // position of component 0 of block (c, r) in uvals; components 32 apart),
+  // chunked like the full storage's columns; padding points at a zero block
+  // after the last entry.
   const T* uvals;
   const int32_t* ucols;
   const int32_t* uslice_len;
@@ -339,20 +340,20 @@ __device__ __forceinline__ void row_product_prefetch(const DevProblem<T>& P, int
   }
 }
 
-// Block-row product from the symmetric storage: the row's entries c < r are
-// the transposes of blocks (c, r) stored with row c, read back through L2
-// (their first reader brought them from HBM); then its entries c >= r.  The
-// entries are summed in the same order (ascending column) with the same
-// operations as row_product, so the result is bitwise the same.
+// Block-row product from the symmetric storage.  The upper structure keeps
+// each entry lane-contiguous -- values [9][32], columns [32] -- so that both
+// its owner row and a row reading the block transposed (whose lanes map to
+// consecutive rows c) load whole 128-byte lines.  The row's entries c < r
+// come first, read back through L2 (their first reader brought them from
+// HBM), then its entries c >= r; same order and operations as row_product,
+// so the sum is bitwise the same.
 template <typename T>
 __device__ __forceinline__ void lower_entry(const DevProblem<T>& P, int c, int pos, const Vec4<T>* vin,
                                             T& a0, T& a1, T& a2) {
-  constexpr int VW = Chunk<T>::VW;
-  const T* b = P.uvals + (pos >> 1);
-  const int st = (pos & 1) ? 32 : 32 * VW;
+  const T* b = P.uvals + pos;
   T m[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) m[q] = __ldcg(b + q * st);
+  for (int q = 0; q < 9; ++q) m[q] = __ldcg(b + q * 32);
   const Vec4<T> x = ldv(vin + c);
   // (A_rc)_ij = (A_cr)_ji
   a0 = fma(m[0], x.x, fma(m[3], x.y, fma(m[6], x.z, a0)));
@@ -387,39 +388,14 @@ __device__ __forceinline__ void row_product_sym(const DevProblem<T>& P, int slic
   }
   const int len = P.uslice_len[slice];
   const int64_t off = P.uslice_off[slice];
-  const T* __restrict__ vb = P.uvals + off * 288;
-  const int32_t* __restrict__ cb = P.ucols + off * 32;
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int nfull = len / VW;
-#pragma unroll 1
-  for (int k = 0; k < nfull; ++k) {
-    int c[VW];
-    T m[9][VW];
-    Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
-    const T* p = vb + (int64_t)k * (288 * VW) + lane * VW;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {   // kept in L2 for the rows below that read them transposed
-      const V x = __ldcg(reinterpret_cast<const V*>(p + q * (32 * VW)));
-      const T* xp = reinterpret_cast<const T*>(&x);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) m[q][e] = xp[e];
-    }
-#pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      const Vec4<T> x = ldv(vin + c[e]);
-      a0 = fma(m[0][e], x.x, fma(m[1][e], x.y, fma(m[2][e], x.z, a0)));
-      a1 = fma(m[3][e], x.x, fma(m[4][e], x.y, fma(m[5][e], x.z, a1)));
-      a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
-    }
-  }
-  const int ntail = len - nfull * VW;
-  const T* pt = vb + (int64_t)nfull * (288 * VW) + lane;
-  const int32_t* ct = cb + (int64_t)nfull * (32 * VW) + lane;
-  for (int t = 0; t < ntail; ++t) {
-    const int c = __ldcs(ct + t * 32);
+  const T* __restrict__ vb = P.uvals + off * 288 + lane;
+  const int32_t* __restrict__ cb = P.ucols + off * 32 + lane;
+#pragma unroll 2
+  for (int e = 0; e < len; ++e) {
+    const int c = __ldcs(cb + e * 32);
     T m[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) m[q] = __ldcg(pt + t * 288 + q * 32);
+    for (int q = 0; q < 9; ++q) m[q] = __ldcg(vb + (int64_t)e * 288 + q * 32);   // kept in L2
     const Vec4<T> x = ldv(vin + c);
     a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
     a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
@@ -1996,7 +1972,7 @@ __global__ void k_fill_sym_pad(int n_slices, const int32_t* __restrict__ ulen,
   for (int k = lane; k < ulen[s] * 32; k += 32) ucols[uoff[s] * 32 + k] = s * 32;
   for (int k = lane; k < llen[s] * 32; k += 32) {
     lcols[loff[s] * 32 + k] = s * 32;
-    lpos[loff[s] * 32 + k] = (int32_t)(((zero + (k & 31)) << 1) | 1);
+    lpos[loff[s] * 32 + k] = (int32_t)(zero + (k & 31));
   }
 }
 
@@ -2014,13 +1990,11 @@ __global__ void k_scatter_upper(int N, const int32_t* __restrict__ row_ptr,
   const int s = p >> 5, lane = p & 31;
   const int r0 = row_ptr[i] + nlow[i], r1 = row_ptr[i + 1];
   for (int e = 0; e < r1 - r0; ++e) {
-    int64_t vp;
-    int vs;
-    const int64_t cp = slot_pos<T>(uoff[s], ulen[s], e, lane, &vp, &vs);
-    if (store_cols) ucols[cp] = node_map[col_idx[r0 + e]];
+    const int64_t ent = uoff[s] + e;
+    if (store_cols) ucols[ent * 32 + lane] = node_map[col_idx[r0 + e]];
     const T* src = vals + (int64_t)(r0 + e) * 9;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) uvals[vp + (int64_t)q * vs] = src[q];
+    for (int q = 0; q < 9; ++q) uvals[ent * 288 + q * 32 + lane] = src[q];
   }
 }
 
@@ -2042,12 +2016,11 @@ __global__ void k_build_lower(int N, const int32_t* __restrict__ row_ptr,
     if (f < 0) { atomicOr(err, 32); return; }
     const int u = f - row_ptr[c] - nlow[c];   // i > c: among row c's entries >= c
     const int pc = node_map[c];
-    int64_t vp, vp2;
-    int vs, vs2;
-    slot_pos<T>(uoff[pc >> 5], ulen[pc >> 5], u, pc & 31, &vp, &vs);
+    int64_t vp2;
+    int vs2;
     const int64_t cp = slot_pos<T>(loff[s], llen[s], j, lane, &vp2, &vs2);
     lcols[cp] = pc;
-    lpos[cp] = (int32_t)((vp << 1) | (vs == 32 ? 1 : 0));
+    lpos[cp] = (int32_t)((uoff[pc >> 5] + u) * 288 + (pc & 31));
   }
 }
 
