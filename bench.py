@@ -38,7 +38,10 @@ FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM traffic (read + write bytes per sweep) of the solve kernel, keyed by
 # the hash of the CUDA sources it was captured from; stale entries read as null.
-NCU_TRAFFIC = {"5b71db1b5c86f019": 553196126}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
+ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
+ADJ_L_MAX = 5000
+ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
+NCU_TRAFFIC = {"25c46a1774b9b41a": 553304650}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
 
 
 def source_hash() -> str:
@@ -303,11 +306,17 @@ def adjoint_bench(args, torch, dev, stream):
     """256 rest-linearised 16x16x8 lattices (6,144 DOF each), a 64-step rollout
     differentiated by torch autograd through the adjoint kernel, checkpointed
     every 8 steps: wall time of the backward pass (recompute + adjoint solves)
-    over the forward pass."""
+    over the forward pass.  The adjoint solves stop relative to their load
+    (dL/dv has the loss's scale) and use Alg. 3; a directional central
+    difference of the loss checks the gradient."""
     from paper_2201_09212_gb300 import scenes, vfpi
     from paper_2201_09212_gb300.autograd import LatticeHarness, rollout
     sc = scenes.lattice_batch(args.adj_scenes, seed=scenes.SEED_BASE + 5, dims=(16, 16, 8))
     s = vfpi.Solver.from_scene(sc, theta_th=THETA_TH, l_max=L_MAX, norm="rms", stream=stream)
+    # the adjoint's load dL/dv has the loss's scale: stop relative to it, and
+    # accelerate the (linear) adjoint iteration with Alg. 3
+    s.set_adjoint_tolerance(ADJ_THETA_REL, ADJ_L_MAX, relative=True)
+    s.set_adjoint_chebyshev(*ADJ_CHEBYSHEV)
     H = LatticeHarness(sc, dev)
     res = {}
     with torch.cuda.stream(stream):
@@ -326,10 +335,26 @@ def adjoint_bench(args, torch, dev, stream):
             t2 = time.perf_counter()
             res = {"forward_s": t1 - t0, "backward_s": t2 - t1,
                    "grad_norm_v0": float(v0.grad.norm()), "grad_norm_mu": float(mu.grad.norm())}
+        # directional central difference of the loss against the gradient
+        d = torch.from_numpy(np.random.default_rng(7).normal(0, 1, sc.n).astype(np.float32)).to(dev)
+        d /= d.abs().max()
+        eps = 1e-4
+        with torch.no_grad():
+            lp = []
+            for sgn in (1.0, -1.0):
+                x, _ = rollout(s, H, H.x_rest.clone(), torch.from_numpy(sc.v0).to(dev) + sgn * eps * d,
+                               torch.from_numpy(sc.mu).to(dev), args.adj_steps, checkpoint=0)
+                lp.append(float(H.com_z(x).sum()))
+        fd = (lp[0] - lp[1]) / (2 * eps)
+        ad = float((v0.grad * d).sum())
+        res["fd_check_v0"] = {"direction": "N(0,1) scaled to max 1", "eps": eps, "fd": fd, "adjoint": ad,
+                              "rel_err": abs(fd - ad) / max(abs(ad), 1e-300)}
     s.close()
     return {
         "workload": f"{args.adj_scenes} lattices 16x16x8 ({6144 * args.adj_scenes} DOF), "
                     f"{args.adj_steps}-step rollout, checkpoint every 8, d(COM z)/d(v0, mu)",
+        "adjoint_solve": {"theta_rel": ADJ_THETA_REL, "l_max": ADJ_L_MAX,
+                          "chebyshev_ls_u": list(ADJ_CHEBYSHEV)},
         "adjoint_forward_ratio": res["backward_s"] / res["forward_s"],
         **res,
     }

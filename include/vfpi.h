@@ -305,6 +305,26 @@ vfpi_status vfpi_set_barzilai_borwein(vfpi_t ctx, int32_t rule, double alpha0);
  * W and the adjoint are unchanged. */
 vfpi_status vfpi_set_chebyshev(vfpi_t ctx, int32_t l_s, double u);
 
+/* The same acceleration (Alg. 3) for the adjoint solve of vfpi_adjoint, set
+ * apart from the forward solve's: the adjoint iteration is linear at the
+ * frozen active set and has the spectrum of the forward iteration's
+ * linearisation, so the semi-iteration applies to it as it stands.  l_s = 0
+ * (the default) switches it off; else l_s >= 3 and 0 < u <= 1.  The adjoint's
+ * fixed point is unchanged.  There is no counterpart in the paper, which does
+ * not differentiate the solve. */
+vfpi_status vfpi_set_adjoint_chebyshev(vfpi_t ctx, int32_t l_s, double u);
+
+/* Stop test of the adjoint solves (vfpi_adjoint), set apart from the
+ * forward's: stop when theta = ||u^{l+1} - u^l|| < theta_th, or with
+ * relative = 1 when theta < theta_th * ||g_v|| (both in the context's norm,
+ * per scene), or at l = l_max (>= 1).  The adjoint's load g_v = dL/dv has the
+ * loss's scale, which an absolute threshold set for velocities does not know;
+ * with the relative test the iterates scale with g_v exactly (a power-of-two
+ * factor gives bitwise scaled results).  Until this is called the adjoint uses
+ * the forward's theta_th and l_max (absolute).  There is no counterpart in
+ * the paper, which does not differentiate the solve. */
+vfpi_status vfpi_set_adjoint_tolerance(vfpi_t ctx, double theta_th, int32_t l_max, int32_t relative);
+
 /* ------------------------------------------------------------------------
  * Allocation-free solve.  The paper has no counterpart to this entry point.
  *

@@ -910,7 +910,8 @@ vfpi_status vfpi_adjoint(vfpi_t c, const void* lambda_star, const void* g_v, voi
   VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dg, c->d_adj_g)));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_adj_u0, 0, vec, c->stream));
   VFPI_TRY_CUDA(cudaMemsetAsync(c->d_adj_u1, 0, vec, c->stream));
-  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, true)));
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->adj_tol_set ? c->adj_l_max : c->opts.l_max,
+                                   c->adj_tol_set ? c->adj_theta_th : c->opts.theta_th, true)));
   vfpi_status run = vfpi_get_status(c, iters_out, theta_out);
   if (run < 0) return run;
   vfpi_status st;
@@ -1144,6 +1145,26 @@ vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
     return arg_fail(c, VFPI_ERR_UNSUPPORTED, "Barzilai-Borwein steps and Chebyshev acceleration exclude each other");
   c->opts.chebyshev_ls = l_s;
   c->opts.chebyshev_u = u;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_adjoint_chebyshev(vfpi_t c, int32_t l_s, double u) {
+  CTX_CHECK(c);
+  if (l_s != 0 && (l_s < 3 || !(u > 0 && u <= 1)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  c->adj_cheb_ls = l_s;
+  c->adj_cheb_u = u;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_adjoint_tolerance(vfpi_t c, double theta_th, int32_t l_max, int32_t relative) {
+  CTX_CHECK(c);
+  if (l_max < 1) return arg_fail(c, VFPI_ERR_INVALID_ARG, "l_max must be >= 1");
+  if (relative != 0 && relative != 1) return arg_fail(c, VFPI_ERR_INVALID_ARG, "relative must be 0 or 1");
+  c->adj_tol_set = 1;
+  c->adj_theta_th = theta_th;
+  c->adj_l_max = l_max;
+  c->adj_rel = relative;
   return VFPI_OK;
 }
 

@@ -118,6 +118,7 @@ struct SolveCtl {
                                  //   words, zero at launch (cluster path)
   int32_t cache_entries;         // sliced-ELL entries one CTA holds in shared memory (cluster path)
   int32_t smem_bytes;            // dynamic shared memory per CTA (cluster path)
+  int32_t theta_rel;             // 1: stop at theta < theta_th * ||b|| (same norm; adjoint)
 };
 
 // alpha_l from the three dot products (Sec. IV.C); the previous value stays
@@ -619,7 +620,7 @@ __device__ __forceinline__ double finish_row_core(const DevProblem<T>& P, int ro
       stv(P.lam_star + cs, ls);
     }
   }
-  if constexpr (!ADJ) vn = cheb_combine(ch, vn, vo, out);   // *out holds v^{l-1}
+  vn = cheb_combine(ch, vn, vo, out);   // *out holds v^{l-1} (u^{l-1} in the adjoint)
   stv(out, vn);
   return sqdiff(vn, vo);
 }
@@ -752,10 +753,8 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
     stv(P.lam_star + cs, ls);
   }
   const Vec4<T> oi = ldv(vin + i), oj = ldv(vin + j);
-  if constexpr (!ADJ) {
-    ni = cheb_combine(ch, ni, oi, vout + i);
-    nj = cheb_combine(ch, nj, oj, vout + j);
-  }
+  ni = cheb_combine(ch, ni, oi, vout + i);
+  nj = cheb_combine(ch, nj, oj, vout + j);
   stv(vout + i, ni);
   stv(vout + j, nj);
   return sqdiff(ni, oi) + sqdiff(nj, oj);
@@ -817,6 +816,46 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
   return *s_ok != 0;
 }
 
+// Threshold of the stop test: theta_th, or theta_th * ||b|| in the same norm
+// when the tolerance is relative to the load (the adjoint, whose b = dL/dv
+// has the loss's arbitrary scale).  Grid-wide form: one extra barrier, the
+// FP64 partials summed in CTA order (parity-0 slots, next written by sweep
+// 2); false if the barrier wait ran out.
+template <typename T, int NT>
+__device__ __forceinline__ bool grid_threshold(const DevProblem<T>& P, const SolveCtl& ctl, int gw,
+                                               int nw, int lane, double* red, int* s_ok,
+                                               double& th) {
+  th = ctl.theta_th;
+  if (!ctl.theta_rel) return true;
+  double acc = 0.0;
+  for (int s = gw; s < P.n_slices; s += nw) {
+    const Vec4<T> g = ldv(P.b + s * 32 + lane);
+    acc += (double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z;
+  }
+  acc = block_allreduce<NT>(acc, red);
+  if (threadIdx.x == 0) ctl.partials[blockIdx.x] = acc;
+  if (!grid_barrier(ctl.bar, s_ok)) return false;
+  double s2 = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += ctl.partials[q];
+  s2 = block_allreduce<NT>(s2, red);
+  th *= sqrt(s2) * ctl.norm_scale[0];
+  return true;
+}
+
+// Per-scene form over slices [s0, s1), computed alike by every CTA that reads it.
+template <typename T, int NT>
+__device__ __forceinline__ double scene_threshold(const DevProblem<T>& P, const SolveCtl& ctl, int s0,
+                                                  int s1, double nscale, double* red) {
+  if (!ctl.theta_rel) return ctl.theta_th;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (s1 - s0) * 32; i += NT) {
+    const Vec4<T> g = ldv(P.b + s0 * 32 + i);
+    acc += (double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z;
+  }
+  acc = block_allreduce<NT>(acc, red);
+  return ctl.theta_th * sqrt(acc) * nscale;
+}
+
 // ---------------------------------------------------------------------------
 // solve kernels
 // ---------------------------------------------------------------------------
@@ -834,11 +873,14 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
-  for (;; ++l) {
+  double th_stop;
+  const bool go = grid_threshold<T, NT>(P, ctl, gw, nw, lane, red, &s_ok, th_stop);
+  if (!go) st = ST_TIMEOUT;
+  for (; go; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
     nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
@@ -900,7 +942,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < ctl.theta_th) { st = ST_OK; break; }
+    if (theta < th_stop) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
@@ -1046,11 +1088,14 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
-  for (;; ++l) {
+  double th_stop;
+  const bool go = grid_threshold<T, NT>(P, ctl, gw, nw, lane, red, &s_ok, th_stop);
+  if (!go) st = ST_TIMEOUT;
+  for (; go; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
     nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
@@ -1150,7 +1195,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < ctl.theta_th) { st = ST_OK; break; }
+    if (theta < th_stop) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1188,13 +1233,14 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
     const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
     const double nscale = ctl.norm_scale[sc];
+    const double th_stop = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
     double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
     for (;; ++l) {
       const Vec4<T>* vin = cur ? P.v1 : P.v0;
       Vec4<T>* vout = cur ? P.v0 : P.v1;
       ChebStep<T> ch;
-      ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+      ch.on = ctl.cheb_ls > 0 ? 1 : 0;
       nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
       ch.accel = ch.on && l >= ctl.cheb_ls;
       ch.nu = (T)nu;
@@ -1228,7 +1274,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;
       if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-      if (theta < ctl.theta_th) { st = ST_OK; break; }
+      if (theta < th_stop) { st = ST_OK; break; }
       if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
       if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
       th2 = th1;
@@ -1452,13 +1498,14 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
   }
   const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
   const double nscale = ctl.norm_scale[sc];
+  const double th_stop = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
   int cur = 0, l = 1, status = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
     nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
@@ -1508,7 +1555,7 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
     theta = sqrt(part) * nscale;
     cur ^= 1;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < ctl.theta_th) { status = ST_OK; break; }
+    if (theta < th_stop) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1666,6 +1713,8 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
   }
   if (ec > 0) phase ^= 1u;
   const double nscale = ctl.norm_scale[sc];
+  const double th_stop =
+      scene_threshold<T, NT>(P, ctl, ctl.scene_slice[sc], ctl.scene_slice[sc + 1], nscale, red);
   int l = 1, status = ST_NOT_CONVERGED, fin = 0;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
@@ -1674,7 +1723,7 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
     Vec4<T>* Vn = pb ? V0 : V1;
     if (G > 1 && threadIdx.x == 0) mbar_arrive_expect_tx(mbar_v + nb, (uint32_t)expect);
     ChebStep<T> ch;
-    ch.on = (!ADJ && ctl.cheb_ls > 0) ? 1 : 0;
+    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
     nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
@@ -1725,7 +1774,7 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
     theta = sqrt(part) * nscale;
     fin = nb;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < ctl.theta_th) { status = ST_OK; break; }
+    if (theta < th_stop) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;

@@ -89,6 +89,10 @@ struct vfpi_ctx {
   double* d_partials = nullptr;
   double* d_bbpart = nullptr;               // BB dot-product partials [2][max_grid][3]
   void *d_r0 = nullptr, *d_r1 = nullptr;    // BB residual ping-pong (allocated on use)
+  int adj_cheb_ls = 0;                      // Chebyshev acceleration of the adjoint solve
+  double adj_cheb_u = 1.0;
+  int adj_tol_set = 0, adj_rel = 0, adj_l_max = 0;   // the adjoint's own stop test
+  double adj_theta_th = 0.0;
   int bb_rule = 0;
   double bb_alpha0 = 0.0;
   unsigned int* d_bar = nullptr;

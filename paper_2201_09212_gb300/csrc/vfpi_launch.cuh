@@ -400,14 +400,15 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.theta = c->d_theta;
   ctl.n_d = c->n_d;
   ctl.err = c->d_err;
-  ctl.cheb_ls = adjoint ? 0 : c->opts.chebyshev_ls;
-  ctl.cheb_u = c->opts.chebyshev_u;
+  ctl.cheb_ls = adjoint ? c->adj_cheb_ls : c->opts.chebyshev_ls;
+  ctl.cheb_u = adjoint ? c->adj_cheb_u : c->opts.chebyshev_u;
   ctl.bb_rule = adjoint ? 0 : c->bb_rule;
   ctl.bb_alpha0 = c->bb_alpha0;
   ctl.bb_part = c->d_bbpart;
   ctl.items = c->d_items;
   ctl.cache_entries = c->cache_entries;
   ctl.smem_bytes = (int32_t)c->dyn_smem;
+  ctl.theta_rel = (adjoint && c->adj_tol_set && c->adj_rel) ? 1 : 0;
   // control words: barrier count/generation, error flag, scene queue
   if ((e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess) return e;

@@ -32,6 +32,7 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
             "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
+            "vfpi_set_adjoint_chebyshev", "vfpi_set_adjoint_tolerance",
             "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
             "vfpi_set_barzilai_borwein",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
@@ -103,6 +104,8 @@ def lib():
         "vfpi_configure_launch": (st, [vp, i32, i32, i32]),
         "vfpi_set_tolerance": (st, [vp, C.c_double, i32]),
         "vfpi_set_chebyshev": (st, [vp, i32, C.c_double]),
+        "vfpi_set_adjoint_chebyshev": (st, [vp, i32, C.c_double]),
+        "vfpi_set_adjoint_tolerance": (st, [vp, C.c_double, i32, i32]),
         "vfpi_set_regularization": (st, [vp, vp]),
         "vfpi_set_anisotropic_friction": (st, [vp, vp]),
         "vfpi_set_barzilai_borwein": (st, [vp, i32, C.c_double]),
@@ -405,6 +408,15 @@ class Solver:
 
     def set_chebyshev(self, l_s, u=1.0):
         self._check(self._L.vfpi_set_chebyshev(self._h, int(l_s), float(u)))
+
+    def set_adjoint_chebyshev(self, l_s, u=1.0):
+        """Alg. 3 for the adjoint solves only (l_s = 0: off)."""
+        self._check(self._L.vfpi_set_adjoint_chebyshev(self._h, int(l_s), float(u)))
+
+    def set_adjoint_tolerance(self, theta_th, l_max, relative=True):
+        """Stop test of the adjoint solves: theta < theta_th (* ||g_v|| if relative)."""
+        self._check(self._L.vfpi_set_adjoint_tolerance(self._h, float(theta_th), int(l_max),
+                                                       1 if relative else 0))
 
     def layout(self) -> dict:
         info = (C.c_int64 * 8)()

@@ -90,3 +90,87 @@ def test_batched_adjoint_equals_per_scene():
         assert np.array_equal(gp1, gp[oc:oc + sc.n_c])
         o += sc.n
         oc += sc.n_c
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_adjoint_chebyshev_keeps_the_fixed_point(seed):
+    """Alg. 3 on the adjoint iteration (linear at the frozen active set): the
+    same gradients as the dense FP64 reference (these small problems converge
+    in a few dozen sweeps, too few for the slow start to pay off; the lattice
+    test below checks the saving)."""
+    rng = np.random.default_rng(950 + seed)
+    sc = scenes.random_problem(rng, 60, 10, d_contacts=5, density=0.08, couple=0.3,
+                               mu_range=(0.2, 0.8), phi_scale=1.0)
+    g_v = rng.normal(0, 1, sc.n)
+    ref, g_b, g_phi, g_mu, P = reference(sc, g_v)
+    with vfpi.Solver.from_scene(sc, theta_th=1e-13, l_max=100000) as s:
+        s.solve(sc.v0)
+        gb0, gp0, gm0, it0, _ = s.adjoint(g_v)
+        s.set_adjoint_chebyshev(10, 0.9)
+        gb, gp, gm, it, th = s.adjoint(g_v)
+        s.set_adjoint_chebyshev(0)
+        gb2, _, _, it2, _ = s.adjoint(g_v)
+    assert th < 1e-13 and it <= it0 + 5
+    assert it2 == it0 and np.array_equal(gb2, gb0)
+    assert relmax(gb, g_b) <= 1e-9
+    assert relmax(gp, g_phi) <= 1e-9
+    assert relmax(gm, g_mu) <= 1e-9 or np.abs(g_mu).max() == 0
+
+
+def test_adjoint_chebyshev_batched_f32():
+    lat = scenes.batched_lattices(12, seed=78, side_range=(4, 8))
+    batch = scenes.concat_scenes(lat)
+    # (scaled so that an rms change of 1e-7 stays well above FP32 rounding of
+    # the adjoint iterate, which is about W g_v ~ 40 g_v here)
+    g_v = (1e-3 * np.random.default_rng(2).normal(0, 1, batch.n)).astype(np.float32)
+    with vfpi.Solver.from_scene(batch, theta_th=1e-7, l_max=5000, norm="rms") as s:
+        s.solve(batch.v0)
+        gb0, gp0, gm0, it0, _ = s.adjoint(g_v)
+        s.set_adjoint_chebyshev(10, 0.9)
+        gb, gp, gm, it, _ = s.adjoint(g_v)
+    assert (it0 < 5000).all() and (it < 5000).all()
+    assert it.sum() < it0.sum()
+    assert relmax(gb, gb0) <= 1e-3
+    assert relmax(gp, gp0) <= 1e-3
+
+
+@pytest.mark.parametrize("path,variant", [(2, 0), (1, 7), (2, 19)],
+                         ids=["scene_kernel", "grid_kernel", "cluster_kernel"])
+def test_relative_adjoint_tolerance_scales_exactly(path, variant):
+    """With the stop test relative to ||g_v|| the adjoint iteration is
+    invariant under scaling g_v: a power-of-two factor scales every iterate,
+    hence the result, bit for bit, after the same number of sweeps."""
+    if path == 1:
+        sc = scenes.terrain_lattice(dims=(40, 36, 8))
+    else:
+        sc = scenes.concat_scenes(scenes.batched_lattices(10, seed=5, side_range=(4, 10)))
+    g_v = np.random.default_rng(8).normal(0, 1, sc.n).astype(np.float32)
+    k = np.float32(2.0 ** -20)
+    with vfpi.Solver.from_scene(sc, theta_th=1e-7, l_max=5000, norm="rms", force_path=path,
+                                kernel_variant=variant) as s:
+        s.solve(sc.v0)
+        # (1e-4: the FP32 rounding of the iterate, ~40-200 g_v, sits near 1e-5 ||g_v||)
+        s.set_adjoint_tolerance(1e-4, 5000, relative=True)
+        gb, gp, gm, it, th = s.adjoint(g_v)
+        gb2, gp2, gm2, it2, th2 = s.adjoint(g_v * k)
+        s.set_adjoint_tolerance(1e-4, 5000, relative=False)
+        _, _, _, it_abs, _ = s.adjoint(g_v * k)
+    assert np.all(np.asarray(it) < 5000)
+    assert np.array_equal(it, it2)
+    assert np.array_equal(gb2, gb * k) and np.array_equal(gp2, gp * k) and np.array_equal(gm2, gm * k)
+    assert np.all(np.asarray(it_abs) <= 2)   # the absolute test stops at once on the tiny load
+
+
+def test_relative_adjoint_tolerance_f64_against_dense_reference():
+    rng = np.random.default_rng(977)
+    sc = scenes.random_problem(rng, 60, 10, d_contacts=5, density=0.08, couple=0.3,
+                               mu_range=(0.2, 0.8), phi_scale=1.0)
+    g_v = 1e-7 * rng.normal(0, 1, sc.n)
+    ref, g_b, g_phi, g_mu, P = reference(sc, g_v)
+    with vfpi.Solver.from_scene(sc, theta_th=1e-13, l_max=100000) as s:
+        s.solve(sc.v0)
+        s.set_adjoint_tolerance(1e-13, 100000, relative=True)
+        gb, gp, gm, it, th = s.adjoint(g_v)
+    assert relmax(gb, g_b) <= 1e-9
+    assert relmax(gp, g_phi) <= 1e-9
+    assert relmax(gm, g_mu) <= 1e-9 or np.abs(g_mu).max() == 0
