@@ -126,7 +126,8 @@ void free_all(vfpi_ctx* c) {
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
                   c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
-                  c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos};
+                  c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos,
+                  c->d_thscene, c->d_slicesq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -663,6 +664,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_CUDA(dalloc(&c->d_iters, 4 * (size_t)c->n_scenes));
   CREATE_CUDA(dalloc(&c->d_status, 4 * (size_t)c->n_scenes));
   CREATE_CUDA(dalloc(&c->d_theta, 8 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_thscene, 8 * (size_t)c->n_scenes));
+  CREATE_CUDA(dalloc(&c->d_slicesq, 8 * (size_t)std::max(c->n_slices, 1)));
   CREATE_CUDA(cudaEventCreate(&c->ev0));
   CREATE_CUDA(cudaEventCreate(&c->ev1));
   cudaStream_t st = c->stream;

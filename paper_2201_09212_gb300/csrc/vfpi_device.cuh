@@ -118,8 +118,15 @@ struct SolveCtl {
                                  //   words, zero at launch (cluster path)
   int32_t cache_entries;         // sliced-ELL entries one CTA holds in shared memory (cluster path)
   int32_t smem_bytes;            // dynamic shared memory per CTA (cluster path)
-  int32_t theta_rel;             // 1: stop at theta < theta_th * ||b|| (same norm; adjoint)
+  int32_t theta_rel;             // 1: stop at theta < th_scene[scene] (adjoint, relative test)
+  const double* th_scene;        // [n_scenes] theta_th * ||b|| of the scene, same norm
 };
+
+// Threshold of scene q's stop test, read where it is compared (nothing extra
+// stays live across the sweep loop).
+__device__ __forceinline__ double stop_threshold(const SolveCtl& ctl, int q) {
+  return ctl.theta_rel ? ctl.th_scene[q] : ctl.theta_th;
+}
 
 // alpha_l from the three dot products (Sec. IV.C); the previous value stays
 // when the curvature s.z is not positive.
@@ -816,45 +823,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
   return *s_ok != 0;
 }
 
-// Threshold of the stop test: theta_th, or theta_th * ||b|| in the same norm
-// when the tolerance is relative to the load (the adjoint, whose b = dL/dv
-// has the loss's arbitrary scale).  Grid-wide form: one extra barrier, the
-// FP64 partials summed in CTA order (parity-0 slots, next written by sweep
-// 2); false if the barrier wait ran out.
-template <typename T, int NT>
-__device__ __forceinline__ bool grid_threshold(const DevProblem<T>& P, const SolveCtl& ctl, int gw,
-                                               int nw, int lane, double* red, int* s_ok,
-                                               double& th) {
-  th = ctl.theta_th;
-  if (!ctl.theta_rel) return true;
-  double acc = 0.0;
-  for (int s = gw; s < P.n_slices; s += nw) {
-    const Vec4<T> g = ldv(P.b + s * 32 + lane);
-    acc += (double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z;
-  }
-  acc = block_allreduce<NT>(acc, red);
-  if (threadIdx.x == 0) ctl.partials[blockIdx.x] = acc;
-  if (!grid_barrier(ctl.bar, s_ok)) return false;
-  double s2 = 0.0;
-  for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += ctl.partials[q];
-  s2 = block_allreduce<NT>(s2, red);
-  th *= sqrt(s2) * ctl.norm_scale[0];
-  return true;
-}
-
-// Per-scene form over slices [s0, s1), computed alike by every CTA that reads it.
-template <typename T, int NT>
-__device__ __forceinline__ double scene_threshold(const DevProblem<T>& P, const SolveCtl& ctl, int s0,
-                                                  int s1, double nscale, double* red) {
-  if (!ctl.theta_rel) return ctl.theta_th;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < (s1 - s0) * 32; i += NT) {
-    const Vec4<T> g = ldv(P.b + s0 * 32 + i);
-    acc += (double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z;
-  }
-  acc = block_allreduce<NT>(acc, red);
-  return ctl.theta_th * sqrt(acc) * nscale;
-}
 
 // ---------------------------------------------------------------------------
 // solve kernels
@@ -873,10 +841,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
-  double th_stop;
-  const bool go = grid_threshold<T, NT>(P, ctl, gw, nw, lane, red, &s_ok, th_stop);
-  if (!go) st = ST_TIMEOUT;
-  for (; go; ++l) {
+  for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
@@ -942,7 +907,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < th_stop) { st = ST_OK; break; }
+    if (theta < stop_threshold(ctl, 0)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
@@ -1088,10 +1053,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
-  double th_stop;
-  const bool go = grid_threshold<T, NT>(P, ctl, gw, nw, lane, red, &s_ok, th_stop);
-  if (!go) st = ST_TIMEOUT;
-  for (; go; ++l) {
+  for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
@@ -1195,7 +1157,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < th_stop) { st = ST_OK; break; }
+    if (theta < stop_threshold(ctl, 0)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1233,7 +1195,6 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
     const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
     const double nscale = ctl.norm_scale[sc];
-    const double th_stop = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
     double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
     for (;; ++l) {
@@ -1274,7 +1235,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;
       if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-      if (theta < th_stop) { st = ST_OK; break; }
+      if (theta < stop_threshold(ctl, sc)) { st = ST_OK; break; }
       if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
       if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
       th2 = th1;
@@ -1498,7 +1459,6 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
   }
   const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
   const double nscale = ctl.norm_scale[sc];
-  const double th_stop = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
   int cur = 0, l = 1, status = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
@@ -1555,7 +1515,7 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
     theta = sqrt(part) * nscale;
     cur ^= 1;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < th_stop) { status = ST_OK; break; }
+    if (theta < stop_threshold(ctl, sc)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1713,8 +1673,6 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
   }
   if (ec > 0) phase ^= 1u;
   const double nscale = ctl.norm_scale[sc];
-  const double th_stop =
-      scene_threshold<T, NT>(P, ctl, ctl.scene_slice[sc], ctl.scene_slice[sc + 1], nscale, red);
   int l = 1, status = ST_NOT_CONVERGED, fin = 0;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
@@ -1774,7 +1732,7 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
     theta = sqrt(part) * nscale;
     fin = nb;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < th_stop) { status = ST_OK; break; }
+    if (theta < stop_threshold(ctl, sc)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1959,6 +1917,34 @@ __global__ void k_scatter_blocks(int N, const int32_t* __restrict__ row_ptr,
 #pragma unroll
     for (int q = 0; q < 9; ++q) svals[vp + (int64_t)q * vs] = src[q];
   }
+}
+
+// ---- relative stop test of the adjoint: theta_th * ||b|| per scene ----
+// (b = dL/dv there; computed before the solve so that the solve kernels
+// carry nothing but one load for it)
+
+// FP64 sum of squares of b over each slice (one warp per slice).
+template <typename T>
+__global__ void k_slice_sumsq(int n_slices, const Vec4<T>* __restrict__ b, double* __restrict__ out) {
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (s >= n_slices) return;
+  const Vec4<T> g = ldv(b + s * 32 + (threadIdx.x & 31));
+  const double x = warp_sum((double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z);
+  if ((threadIdx.x & 31) == 0) out[s] = x;
+}
+
+// One CTA per scene: th[q] = theta_th * sqrt(sum of its slices' sums) * norm scale,
+// the slices' sums taken in a fixed order.
+static __global__ void k_scene_threshold(const int32_t* __restrict__ scene_slice,
+                                         const double* __restrict__ slice_sumsq,
+                                         const double* __restrict__ norm_scale, double theta_th,
+                                         double* __restrict__ th) {
+  __shared__ double red[33];
+  const int q = blockIdx.x;
+  double acc = 0.0;
+  for (int s = scene_slice[q] + threadIdx.x; s < scene_slice[q + 1]; s += 256) acc += slice_sumsq[s];
+  acc = block_allreduce<256>(acc, red);
+  if (threadIdx.x == 0) th[q] = theta_th * sqrt(acc) * norm_scale[q];
 }
 
 // ---- symmetric storage set-up (caller's sorted BSR pattern, one scene) ----

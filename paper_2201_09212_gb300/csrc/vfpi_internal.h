@@ -93,6 +93,7 @@ struct vfpi_ctx {
   double adj_cheb_u = 1.0;
   int adj_tol_set = 0, adj_rel = 0, adj_l_max = 0;   // the adjoint's own stop test
   double adj_theta_th = 0.0;
+  double *d_slicesq = nullptr, *d_thscene = nullptr;  // relative test: [n_slices], [n_scenes]
   int bb_rule = 0;
   double bb_alpha0 = 0.0;
   unsigned int* d_bar = nullptr;

@@ -9,8 +9,10 @@ CTAs (all that fit, the fewest that keep the same slices per warp, whole
 multiples of the SM count); for batched scenes: the threads per CTA of the
 CTA-per-scene kernel (warps working on one scene) and the shapes of the
 shared-memory-resident cluster kernel (threads per CTA, CTAs per cluster, CTAs
-per SM) -- each over a fixed number of sweeps of the solver's own problem,
-timed with CUDA events, and keeps the fastest.  Results
+per SM) -- the grid kernel over a fixed number of sweeps, batched scenes over
+whole solves at the solver's tolerance (their uneven iteration counts decide
+the load balance), on the solver's own problem, timed with CUDA events, and
+keeps the fastest.  Results
 are cached in a JSON file keyed by the layout signature and the GPU name, so a
 later solver of the same shape reuses them without timing.
 """
@@ -44,9 +46,11 @@ def _grid_candidates(n_slices, warps, max_grid, sms):
     return sorted(g for g in out if g == 0 or g <= max_grid)
 
 
-def _time(solver, sweeps, reps):
+def _time(solver, sweeps, reps, v_start=None):
     best = float("inf")
     for _ in range(reps):
+        if v_start is not None:
+            solver.set_velocity(v_start)
         solver.solve_async()
         solver.status()
         best = min(best, solver.last_kernel_ms())
@@ -87,22 +91,30 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
                 trials.append(dict(kernel_variant=var, block_threads=0, grid_ctas=g,
                                    ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
     else:
+        # batched scenes converge after different numbers of sweeps, which
+        # decides the load balance: time whole solves at the solver's own
+        # tolerance from the same warm start
+        solver.set_tolerance(theta0, lmax0)
+        v_start = solver.get_velocity()
         shapes = [(0, bt) for bt in (64, 128, 256)] + [(v, 0) for v in CLUSTER_VARIANTS]
         for var, bt in shapes:
             try:
                 solver.configure_launch(var, bt, 0)
             except RuntimeError:    # shape not available on this GPU
                 continue
-            ms = _time(solver, sweeps, reps)
+            ms = _time(solver, sweeps, reps, v_start)
+            iters, _, _ = solver.status()
             trials.append(dict(kernel_variant=var, block_threads=bt, grid_ctas=0,
-                               ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
+                               ms_per_sweep=ms / max(1.0, float(iters.max())), ms_per_solve=ms,
+                               grid=solver.layout()["grid"]))
+        solver.set_velocity(v_start)
     solver.set_tolerance(theta0, lmax0)
-    best = min(trials, key=lambda t: t["ms_per_sweep"])
+    best = min(trials, key=lambda t: t.get("ms_per_solve", t["ms_per_sweep"]))
     solver.configure_launch(best["kernel_variant"], best["block_threads"], best["grid_ctas"])
     result = dict(best, trials=trials)
     if cache:
         table[key] = {k: best[k] for k in ("kernel_variant", "block_threads", "grid_ctas",
-                                           "ms_per_sweep", "grid")}
+                                           "ms_per_sweep", "grid") if k in best}
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         with open(cache, "w") as f:
             json.dump(table, f, indent=1)

@@ -174,3 +174,29 @@ def test_relative_adjoint_tolerance_f64_against_dense_reference():
     assert relmax(gb, g_b) <= 1e-9
     assert relmax(gp, g_phi) <= 1e-9
     assert relmax(gm, g_mu) <= 1e-9 or np.abs(g_mu).max() == 0
+
+
+def test_relative_adjoint_tolerance_is_per_scene():
+    """Each scene of a batch stops on its own load's norm: with loads of very
+    different sizes the batched adjoint equals each scene's own solve bit for
+    bit (one shared threshold would change the iteration counts)."""
+    lat = scenes.batched_lattices(6, seed=31, side_range=(4, 8))
+    batch = scenes.concat_scenes(lat)
+    rng = np.random.default_rng(12)
+    parts = [(rng.normal(0, 1, sc.n) * 2.0 ** (-6 * q)).astype(np.float32) for q, sc in enumerate(lat)]
+    g_v = np.concatenate(parts)
+    with vfpi.Solver.from_scene(batch, theta_th=1e-7, l_max=5000, norm="rms", block_threads=128) as s:
+        s.solve(batch.v0)
+        s.set_adjoint_tolerance(1e-4, 5000, relative=True)
+        gb, gp, gm, its, _ = s.adjoint(g_v)
+    assert (its < 5000).all() and len(set(its.tolist())) > 1
+    o = 0
+    for q, sc in enumerate(lat):
+        with vfpi.Solver.from_scene(sc, theta_th=1e-7, l_max=5000, norm="rms", block_threads=128,
+                                    force_path=2) as s1:
+            s1.solve(sc.v0)
+            s1.set_adjoint_tolerance(1e-4, 5000, relative=True)
+            gb1, _, _, it1, _ = s1.adjoint(parts[q])
+        assert it1 == its[q], q
+        assert np.array_equal(gb1, gb[o:o + sc.n]), q
+        o += sc.n
