@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
 ADJ_L_MAX = 5000
 ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
-NCU_TRAFFIC = {"a4c3a8c3430c70c5": 553391185}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
+NCU_TRAFFIC = {"f117c23d451ded58": 553317190}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
 
 
 def source_hash() -> str:
@@ -317,6 +317,9 @@ def adjoint_bench(args, torch, dev, stream):
     # accelerate the (linear) adjoint iteration with Alg. 3
     s.set_adjoint_tolerance(ADJ_THETA_REL, ADJ_L_MAX, relative=True)
     s.set_adjoint_chebyshev(*ADJ_CHEBYSHEV)
+    s.set_velocity(torch.from_numpy(sc.v0).to(dev))
+    from paper_2201_09212_gb300 import tune
+    tuned = tune.tune(s, sweeps=20, reps=2)
     H = LatticeHarness(sc, dev)
     res = {}
     with torch.cuda.stream(stream):
@@ -360,6 +363,7 @@ def adjoint_bench(args, torch, dev, stream):
                     f"{args.adj_steps}-step rollout, checkpoint every 8, d(COM z)/d(v0, mu)",
         "adjoint_solve": {"theta_rel": ADJ_THETA_REL, "l_max": ADJ_L_MAX,
                           "chebyshev_ls_u": list(ADJ_CHEBYSHEV)},
+        "launch": {k: tuned[k] for k in ("kernel_variant", "block_threads", "grid")},
         "adjoint_forward_ratio": res["backward_s"] / res["forward_s"],
         **res,
     }

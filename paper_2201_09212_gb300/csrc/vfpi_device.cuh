@@ -118,15 +118,10 @@ struct SolveCtl {
                                  //   words, zero at launch (cluster path)
   int32_t cache_entries;         // sliced-ELL entries one CTA holds in shared memory (cluster path)
   int32_t smem_bytes;            // dynamic shared memory per CTA (cluster path)
-  int32_t theta_rel;             // 1: stop at theta < th_scene[scene] (adjoint, relative test)
-  const double* th_scene;        // [n_scenes] theta_th * ||b|| of the scene, same norm
+  int32_t theta_rel;             // 1: the adjoint stops at theta < theta_th * ||b|| (same norm)
+  const double* th_scene;        // grid path: [1] theta_th * ||b||, computed before the launch
 };
 
-// Threshold of scene q's stop test, read where it is compared (nothing extra
-// stays live across the sweep loop).
-__device__ __forceinline__ double stop_threshold(const SolveCtl& ctl, int q) {
-  return ctl.theta_rel ? ctl.th_scene[q] : ctl.theta_th;
-}
 
 // alpha_l from the three dot products (Sec. IV.C); the previous value stays
 // when the curvature s.z is not positive.
@@ -823,6 +818,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
   return *s_ok != 0;
 }
 
+// Stop threshold of a scene's adjoint solve over slices [s0, s1): theta_th, or
+// with the relative test theta_th * ||b|| (b = dL/dv, same norm), the sum of
+// squares taken in one fixed order by every CTA that reads the scene.  (The
+// forward instantiations compare against theta_th directly.)
+template <typename T, int NT>
+__device__ __forceinline__ double scene_threshold(const DevProblem<T>& P, const SolveCtl& ctl, int s0,
+                                                  int s1, double nscale, double* red) {
+  if (!ctl.theta_rel) return ctl.theta_th;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (s1 - s0) * 32; i += NT) {
+    const Vec4<T> g = ldv(P.b + s0 * 32 + i);
+    acc += (double)g.x * g.x + (double)g.y * g.y + (double)g.z * g.z;
+  }
+  acc = block_allreduce<NT>(acc, red);
+  return ctl.theta_th * sqrt(acc) * nscale;
+}
+
 
 // ---------------------------------------------------------------------------
 // solve kernels
@@ -907,7 +919,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < stop_threshold(ctl, 0)) { st = ST_OK; break; }
+    if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
@@ -1157,7 +1169,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-    if (theta < stop_threshold(ctl, 0)) { st = ST_OK; break; }
+    if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1195,6 +1207,8 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     const int s0 = ctl.scene_slice[sc], s1 = ctl.scene_slice[sc + 1];
     const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
     const double nscale = ctl.norm_scale[sc];
+    double th_adj = 0.0;
+    if constexpr (ADJ) th_adj = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
     double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
     for (;; ++l) {
@@ -1235,7 +1249,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
       theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
       cur ^= 1;
       if (!isfinite(theta)) { st = ST_NONFINITE; break; }
-      if (theta < stop_threshold(ctl, sc)) { st = ST_OK; break; }
+      if (theta < (ADJ ? th_adj : ctl.theta_th)) { st = ST_OK; break; }
       if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
       if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
       th2 = th1;
@@ -1459,6 +1473,8 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
   }
   const int d0 = ctl.scene_d[sc], d1 = ctl.scene_d[sc + 1];
   const double nscale = ctl.norm_scale[sc];
+  double th_adj = 0.0;
+  if constexpr (ADJ) th_adj = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
   int cur = 0, l = 1, status = ST_NOT_CONVERGED;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
@@ -1515,7 +1531,7 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
     theta = sqrt(part) * nscale;
     cur ^= 1;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < stop_threshold(ctl, sc)) { status = ST_OK; break; }
+    if (theta < (ADJ ? th_adj : ctl.theta_th)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;
@@ -1673,6 +1689,9 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
   }
   if (ec > 0) phase ^= 1u;
   const double nscale = ctl.norm_scale[sc];
+  double th_adj = 0.0;
+  if constexpr (ADJ)
+    th_adj = scene_threshold<T, NT>(P, ctl, ctl.scene_slice[sc], ctl.scene_slice[sc + 1], nscale, red);
   int l = 1, status = ST_NOT_CONVERGED, fin = 0;
   double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
@@ -1732,7 +1751,7 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
     theta = sqrt(part) * nscale;
     fin = nb;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
-    if (theta < stop_threshold(ctl, sc)) { status = ST_OK; break; }
+    if (theta < (ADJ ? th_adj : ctl.theta_th)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
     if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
     th2 = th1;

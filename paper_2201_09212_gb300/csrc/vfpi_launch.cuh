@@ -410,7 +410,7 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.smem_bytes = (int32_t)c->dyn_smem;
   ctl.theta_rel = (adjoint && c->adj_tol_set && c->adj_rel) ? 1 : 0;
   ctl.th_scene = c->d_thscene;
-  if (ctl.theta_rel && c->n_slices > 0) {
+  if (ctl.theta_rel && c->path == 1 && c->n_slices > 0) {   // (the per-scene kernels compute theirs)
     k_slice_sumsq<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
         c->n_slices, static_cast<const Vec4<T>*>(c->d_adj_g), c->d_slicesq);
     k_scene_threshold<<<c->n_scenes, 256, 0, s>>>(c->d_scene_slice, c->d_slicesq, c->d_norm_scale,
