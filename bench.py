@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
 ADJ_L_MAX = 5000
 ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
-NCU_TRAFFIC = {"f117c23d451ded58": 553317190}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
+NCU_TRAFFIC = {"f98a1874a8756517": 553349525}   # profiles/k_solve_grid_terrain_lattice_128x128x32.md
 
 
 def source_hash() -> str:
