@@ -116,6 +116,8 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
         table[key] = {k: best[k] for k in ("kernel_variant", "block_threads", "grid_ctas",
                                            "ms_per_sweep", "grid") if k in best}
         os.makedirs(os.path.dirname(cache), exist_ok=True)
-        with open(cache, "w") as f:
+        tmp = f"{cache}.{os.getpid()}.tmp"       # several ranks may tune at once
+        with open(tmp, "w") as f:
             json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
     return dict(result, cached=False)
