@@ -96,7 +96,7 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
         # tolerance from the same warm start
         solver.set_tolerance(theta0, lmax0)
         v_start = solver.get_velocity()
-        shapes = [(0, bt) for bt in (64, 128, 256)] + [(v, 0) for v in CLUSTER_VARIANTS]
+        shapes = [(0, bt) for bt in (64, 128, 256, 512)] + [(v, 0) for v in CLUSTER_VARIANTS]
         for var, bt in shapes:
             try:
                 solver.configure_launch(var, bt, 0)
