@@ -176,3 +176,19 @@ def test_cluster_shapes_need_the_scene_path():
             s.configure_launch(19, 0, 0)
         r = s.solve(sc.v0)            # the previous shape still works
         assert np.isfinite(r.theta)
+
+
+def test_batched_tuner_times_whole_solves_and_restores_the_warm_start(uneven, tmp_path):
+    from paper_2201_09212_gb300 import tune
+    batch = scenes.concat_scenes(uneven[:16])
+    ref, _ = run(batch, 0, 256)
+    with vfpi.Solver.from_scene(batch, theta_th=1e-6, l_max=300) as s:
+        s.set_velocity(batch.v0)
+        res = tune.tune(s, sweeps=5, reps=1, cache=str(tmp_path / "t.json"))
+        assert not res["cached"]
+        shapes = {(t["kernel_variant"], t["block_threads"]) for t in res["trials"]}
+        assert {(0, 64), (0, 128), (0, 256), (0, 512)} <= shapes and (19, 0) in shapes
+        assert all("ms_per_solve" in t for t in res["trials"])
+        assert np.array_equal(s.get_velocity(), batch.v0)      # warm start put back
+        r = s.solve(batch.v0)
+    assert np.array_equal(r.iters, ref.iters) and np.array_equal(r.v, ref.v)
