@@ -75,7 +75,9 @@ enum { VFPI_NORM_ABS = 0, VFPI_NORM_RMS = 1 };
 /* A in 3x3 block-sparse-row form (Sec. V.A stores A sparse; blocks here).
  * row_ptr [n_nodes+1], col_idx [nnzb] strictly increasing per row with the
  * diagonal block present, vals [nnzb * 9] row-major blocks.  The full
- * (symmetric) pattern is given; no symmetry is assumed by the solver. */
+ * (symmetric) pattern is given; the solver assumes no symmetry of the values,
+ * and offers the symmetric-storage launch shapes only when create or update
+ * finds A = A^T bit for bit. */
 typedef struct {
   int32_t n_nodes;
   int32_t nnzb;
@@ -111,10 +113,11 @@ typedef struct {
   const int32_t* scene_ptr;/* [n_scenes+1] node offsets of the scenes (batched)     */
   int32_t block_threads;   /* 0 = default; threads per CTA of the solve kernel       */
   int32_t force_path;      /* 0 = auto, 1 = grid-wide kernel, 2 = CTA-per-scene      */
-  int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..11 (threads per
-                              CTA, CTAs/SM register budget, prefetch, TMA ring);
-                              scene path 0 or VFPI_VARIANT_CL_*; with 0 a nonzero
-                              block_threads selects that CTA size, unbudgeted     */
+  int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..15 (threads per
+                              CTA, CTAs/SM register budget, prefetch, TMA ring,
+                              symmetric storage); scene path 0 or
+                              VFPI_VARIANT_CL_*; with 0 a nonzero block_threads
+                              selects that CTA size, unbudgeted                  */
   int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
                               fit, capped at one warp per 32-row slice)              */
   int32_t chebyshev_ls;    /* Chebyshev acceleration (Alg. 3): slow-start index
@@ -236,8 +239,9 @@ vfpi_status vfpi_get_status(vfpi_t ctx, int32_t* iters_out, double* theta_out);
  * the adjoint g_bar solves (I - (I - S)(I - W A))^T g_bar = g_v; it is found by
  * the transposed sweep iterated on u = W (I - S^T) g_bar -- the forward sweep
  * with b := g_v and the contact step replaced by the frozen linear map
- * u_i -= (w_i / gamma) R^T P'^T R (u*_i - u*_j) -- with the same theta_th and
- * l_max as the forward solve.  Outputs (nullable): g_b = dL/db [3N] (= u at
+ * u_i -= (w_i / gamma) R^T P'^T R (u*_i - u*_j) -- with the forward solve's
+ * theta_th and l_max unless vfpi_set_adjoint_tolerance gave the adjoint its
+ * own stop test, and with Alg. 3 if vfpi_set_adjoint_chebyshev switched it on.  Outputs (nullable): g_b = dL/db [3N] (= u at
  * convergence), g_phi = dL/dphi [n_c] = -(P'^T z)_n / gamma and
  * g_mu = dL/dmu [n_c] = lambda_n t . z_t (slip), z = J_c u*.  Synchronises. */
 vfpi_status vfpi_adjoint(vfpi_t ctx, const void* lambda_star, const void* g_v, void* g_b,
