@@ -38,6 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM traffic (read + write bytes per sweep) of the solve kernel, keyed by
 # the hash of the CUDA sources it was captured from; stale entries read as null.
+BATCH_CHEBYSHEV = (5, 1.0)   # Alg. 3 for the batched env steps' second figure
 ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
 ADJ_L_MAX = 5000
 ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
@@ -242,31 +243,43 @@ def batched_bench(args, torch, dev, stream, rank):
         s.integrate(x)
         s.get_velocity(out=v)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            env_step()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            env_step()
-        for _ in range(2):
-            g.replay()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        dof_iters, kms, its = 0, [], []
-        n_dof = 3 * nq
-        t_total = 0.0
-        for _ in range(args.batch_steps):
-            ev0.record(stream)
-            g.replay()
-            ev1.record(stream)
-            ev1.synchronize()
-            t_total += ev0.elapsed_time(ev1) / 1e3
-            it, _, _ = s.status()
-            its.append(it.copy())
-            dof_iters += int((n_dof * it).sum())
-            kms.append(s.last_kernel_ms())
-    its = np.array(its)
+    n_dof = 3 * nq
+
+    def timed_steps():
+        # from the initial state: warm-up steps, one graph per env step, timed replays
+        x.copy_(x0)
+        v.copy_(T(sc.v0, np.float32))
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                env_step()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                env_step()
+            for _ in range(2):
+                g.replay()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            dof_iters, kms, its = 0, [], []
+            t_total = 0.0
+            for _ in range(args.batch_steps):
+                ev0.record(stream)
+                g.replay()
+                ev1.record(stream)
+                ev1.synchronize()
+                t_total += ev0.elapsed_time(ev1) / 1e3
+                it, _, _ = s.status()
+                its.append(it.copy())
+                dof_iters += int((n_dof * it).sum())
+                kms.append(s.last_kernel_ms())
+        return t_total, np.array(its), dof_iters, kms
+
+    t_total, its, dof_iters, kms = timed_steps()
+    # the same env steps with Chebyshev acceleration (Alg. 3) of the solves:
+    # the same stop test, reached in fewer sweeps
+    s.set_chebyshev(*BATCH_CHEBYSHEV)
+    t_cheb, its_cheb, _, _ = timed_steps()
+    s.set_chebyshev(0)
     env_sps = S * args.batch_steps / t_total
     nc_q = np.bincount(np.searchsorted(sc.scene_ptr, sc.node_i, side="right") - 1, minlength=S)
     bytes_scene = np.array([
@@ -306,6 +319,11 @@ def batched_bench(args, torch, dev, stream, rank):
         "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
                          "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0]},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
+        "with_chebyshev": {"l_s_u": list(BATCH_CHEBYSHEV),
+                           "env_steps_per_s": S * args.batch_steps / t_cheb,
+                           "ms_per_env_step": 1e3 * t_cheb / args.batch_steps,
+                           "iters_per_scene": {"mean": float(its_cheb.mean()),
+                                               "max": int(its_cheb.max())}},
         "per_scene_plain": {"sample": len(sample), "mean_solve_ms": float(np.mean(per_ms)),
                             "extrapolated_all_scenes_s": per_scene_total,
                             "batched_solve_s": first_batch,
