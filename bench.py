@@ -474,6 +474,27 @@ def main():
     value, elapsed, _ = aggregate(dist, dev, elapsed, sc.n * sum(iters))
     launches_per_step = 3  # warm-start conversion, solve, integrate
 
+    # time to solution of the same step with Chebyshev acceleration (Alg. 3):
+    # the sweep is the same kernel, the stop test is reached in fewer sweeps
+    s.set_chebyshev(*BATCH_CHEBYSHEV)
+    for _ in range(3):
+        step()
+        s.status()
+    cheb_iters = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(min(args.steps, 50)):
+        step()
+        cheb_iters.append(int(s.status()[0][0]))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    cheb_ms = ev0.elapsed_time(ev1) / len(cheb_iters)
+    s.set_chebyshev(0)
+    time_to_solution = {"alg1_ms_per_step": 1e3 * elapsed / args.steps,
+                        "alg1_iters_per_step": float(np.mean(iters)),
+                        "alg3_l_s_u": list(BATCH_CHEBYSHEV), "alg3_ms_per_step": cheb_ms,
+                        "alg3_iters_per_step": float(np.mean(cheb_iters))}
+
     # end to end through the public API with pinned host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     b_h, phi_h, v_h, x_h = pin(sc.b), pin(sc.phi), pin(sc.v0), pin(sc.x0)
@@ -552,6 +573,7 @@ def main():
                        f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks"
                        if sym else f"{sc.nnzb * 40 / 1e6:.0f} MB of blocks") + " streamed per sweep)")},
         "roofline": roofline,
+        "time_to_solution": time_to_solution,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
