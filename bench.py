@@ -54,17 +54,13 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes_per_sweep(sc, esz=4, sym=False) -> int:
-    """Bytes one sweep must move at minimum: every block and column index once,
-    the row pointers, v^l read, b read, v^{l+1} written, W read, the contact
-    records (R, mu, phi, node ids: 48 B) and lambda written (12 B).  With the
-    symmetric storage (A = A^T) only the (nnzb + N) / 2 blocks c >= r carry
-    values and a column; the (nnzb - N) / 2 blocks c < r cost their column
-    alone (their values are the transposes read again)."""
+def algorithmic_bytes_per_sweep(sc, esz=4) -> int:
+    """Bytes one sweep must move at minimum with A as given (full BSR): every
+    block and column index once, the row pointers, v^l read, b read, v^{l+1}
+    written, W read, the contact records (R, mu, phi, node ids: 48 B) and
+    lambda written (12 B)."""
     N, n, nnzb, n_c = sc.n_nodes, sc.n, sc.nnzb, sc.n_c
     vec = 4 * (N + 1) + 3 * esz * n + esz * N + n_c * (48 + 12)
-    if sym:
-        return ((nnzb + N) // 2) * (9 * esz + 4) + ((nnzb - N) // 2) * 4 + vec
     return nnzb * (9 * esz + 4) + vec
 
 
@@ -331,6 +327,49 @@ def batched_bench(args, torch, dev, stream, rank):
     }
 
 
+def configs_bench(args, torch, dev, stream):
+    """The other plain-V-FPI configurations, each solved from its initial
+    state repeatedly (tuned launch shape; a 256 MB write between steps flushes
+    L2): the 6x6x6 FP64 lattice and the 64x64x16 FEM block.  The FEM block's
+    matrix (about 45 MB) fits in the 126 MB L2, so within a solve its sweeps
+    run from L2 and the fraction of HBM is an effective one."""
+    from paper_2201_09212_gb300 import scenes, tune, vfpi
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for name, make, dtype, esz, theta, steps in (
+            ("small_lattice_6x6x6_f64", lambda: scenes.small_lattice(np.float64), "f64", 8, 1e-9, 100),
+            ("fem_block_64x64x16_f32", lambda: scenes.fem_block(), "f32", 4, 1e-6, 50)):
+        sc = make()
+        with vfpi.Solver.from_scene(sc, theta_th=theta, l_max=5000, norm="rms", dtype=dtype,
+                                    stream=stream) as s:
+            v0 = torch.from_numpy(sc.v0).to(dev)
+            s.set_velocity(v0)
+            tuned = tune.tune(s, sweeps=20, reps=2)
+            kms, its = [], []
+            with torch.cuda.stream(stream):
+                for k in range(3 + steps):
+                    flush.fill_(float(k))
+                    s.set_velocity(v0)
+                    s.solve_async()
+                    it, _, _ = s.status()
+                    if k >= 3:
+                        kms.append(s.last_kernel_ms())
+                        its.append(int(it[0]))
+            lay = s.layout()
+        t = sum(kms) / 1e3
+        bps = algorithmic_bytes_per_sweep(sc, esz)
+        achieved = bps * sum(its) / t / 1e9
+        out[name] = {"dof": sc.n, "blocks": sc.nnzb, "contacts": sc.n_c, "dtype": dtype,
+                     "theta_th_rms": theta, "steps": steps, "iters_per_step": float(np.mean(its)),
+                     "dof_iters_per_s": sc.n * sum(its) / t, "ms_per_solve": 1e3 * t / steps,
+                     "achieved_gbs": achieved, "frac_of_hbm": achieved / peaks()[0],
+                     "matrix_mb": sc.nnzb * (9 * esz + 4) / 1e6,
+                     "path": "grid" if lay["path"] == 1 else "CTA-per-scene",
+                     "launch": {k: tuned[k] for k in ("kernel_variant", "block_threads", "grid")},
+                     "l2": "flushed between steps (256 MB write)"}
+    return out
+
+
 def adjoint_bench(args, torch, dev, stream):
     """256 rest-linearised 16x16x8 lattices (6,144 DOF each), a 64-step rollout
     differentiated by torch autograd through the adjoint kernel, checkpointed
@@ -414,6 +453,7 @@ def main():
     ap.add_argument("--adj-scenes", type=int, default=256)
     ap.add_argument("--adj-steps", type=int, default=64)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -534,13 +574,19 @@ def main():
     if not args.no_adjoint and rank == 0:
         adjoint = adjoint_bench(args, torch, dev, stream)
 
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = configs_bench(args, torch, dev, stream)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
     sym = 12 <= int(tuned["kernel_variant"]) <= 15
-    bps = algorithmic_bytes_per_sweep(sc, sym=sym)
+    # always the full-BSR count: a compressed storage is reported as an
+    # effective fraction next to the measured DRAM bytes, not by a new count
+    bps = algorithmic_bytes_per_sweep(sc)
     k_avg = float(np.mean(kms)) / 1e3
     it_avg = float(np.mean(iters))
     achieved = bps * it_avg / k_avg / 1e9
@@ -551,7 +597,7 @@ def main():
                 "traffic": (tr * it_avg if tr else None),
                 "algorithmic_bytes_per_sweep": bps,
                 "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
-                          + (" (symmetric storage)" if sym else ""),
+                          + (" (symmetric storage; effective fraction)" if sym else ""),
                 "kernel_ms_avg": 1e3 * k_avg}
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -580,6 +626,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "batched": batched,
         "adjoint": adjoint,
+        "configs": configs,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

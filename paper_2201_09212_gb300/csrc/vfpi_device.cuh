@@ -792,26 +792,32 @@ __device__ __forceinline__ double block_allreduce(double x, double* red) {
 // All CTAs arrive; returns false if the wait ran out (the caller then stops).
 // Co-residency of all CTAs is guaranteed by the cooperative launch; the spin
 // is bounded anyway so that a fault elsewhere can never hang the GPU.
+// Release/acquire at GPU scope: each CTA's arrival (acq_rel) publishes what
+// the CTA wrote before it; the last arrival resets the count and publishes a
+// new generation (release), which the others read with acquire loads, so they
+// see every CTA's writes without a full fence.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = bar + 1;
-    const unsigned int gen = *vgen;
-    __threadfence();
-    const unsigned int ticket = atomicAdd(bar, 1u);
+    const unsigned int gen = ld_acquire_gpu(bar + 1);
+    unsigned int ticket;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(bar) : "memory");
     int ok = 1;
     if (ticket == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
       ok = 0;
       for (long long it = 0; it < kBarrierPolls; ++it) {
-        if (*vgen != gen) { ok = 1; break; }
-        __nanosleep(64);
+        if (ld_acquire_gpu(bar + 1) != gen) { ok = 1; break; }
+        if (it > 64) __nanosleep(32);
       }
     }
-    __threadfence();
     *s_ok = ok;
   }
   __syncthreads();
