@@ -12,7 +12,9 @@ shared-memory-resident cluster kernel (threads per CTA, CTAs per cluster, CTAs
 per SM) -- the grid kernel over a fixed number of sweeps, batched scenes over
 whole solves at the solver's tolerance (their uneven iteration counts decide
 the load balance), on the solver's own problem, timed with CUDA events, and
-keeps the fastest.  Results
+keeps the fastest (a TMA-ring, symmetric-storage or cluster shape only when it
+beats the best plain shape by 2 %, so that timing noise does not switch
+kernels from one GPU to the next).  Results
 are cached in a JSON file keyed by the layout signature and the GPU name, so a
 later solver of the same shape reuses them without timing.
 """
@@ -28,6 +30,7 @@ GRID_VARIANTS = tuple(range(16))      # 12..15 need an exactly symmetric A
 WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2,
          12: 8, 13: 8, 14: 8, 15: 16}
 CLUSTER_VARIANTS = tuple(range(16, 26))
+SPECIAL_MARGIN = 0.02
 
 
 def _signature(solver, gpu: str) -> str:
@@ -109,7 +112,16 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
                                grid=solver.layout()["grid"]))
         solver.set_velocity(v_start)
     solver.set_tolerance(theta0, lmax0)
-    best = min(trials, key=lambda t: t.get("ms_per_solve", t["ms_per_sweep"]))
+    # the special kernels (TMA ring 8-11, symmetric storage 12-15, cluster
+    # 16-25) must beat the best plain shape by SPECIAL_MARGIN: a win inside
+    # the timing noise should not switch kernels from one GPU to the next
+    cost = lambda t: t.get("ms_per_solve", t["ms_per_sweep"])   # noqa: E731
+    plain = [t for t in trials if t["kernel_variant"] < 8]
+    best = min(trials, key=cost)
+    if plain and best["kernel_variant"] >= 8:
+        bp = min(plain, key=cost)
+        if cost(best) > (1.0 - SPECIAL_MARGIN) * cost(bp):
+            best = bp
     solver.configure_launch(best["kernel_variant"], best["block_threads"], best["grid_ctas"])
     result = dict(best, trials=trials)
     if cache:
