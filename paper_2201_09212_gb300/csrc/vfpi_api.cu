@@ -127,7 +127,7 @@ void free_all(vfpi_ctx* c) {
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
                   c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
                   c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos,
-                  c->d_thscene, c->d_slicesq, c->d_scene_entries};
+                  c->d_thscene, c->d_slicesq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -684,14 +684,6 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
     for (int q = 0; q < c->n_scenes; ++q)
       nscale[q] = 1.0 / std::sqrt(3.0 * (c->h_scene_ptr[q + 1] - c->h_scene_ptr[q]));
   CREATE_CUDA(cudaMemcpyAsync(c->d_order, order.data(), 4 * (size_t)c->n_scenes, cudaMemcpyHostToDevice, st));
-  {
-    std::vector<int64_t> ent(c->n_scenes, 0);
-    for (int q = 0; q < c->n_scenes; ++q)
-      for (int sl = c->h_scene_slice[q]; sl < c->h_scene_slice[q + 1]; ++sl) ent[q] += c->h_slice_len[sl];
-    CREATE_CUDA(dalloc(&c->d_scene_entries, 8 * (size_t)c->n_scenes));
-    CREATE_CUDA(cudaMemcpyAsync(c->d_scene_entries, ent.data(), 8 * (size_t)c->n_scenes,
-                                cudaMemcpyHostToDevice, st));
-  }
   CREATE_CUDA(cudaMemcpyAsync(c->d_norm_scale, nscale.data(), 8 * (size_t)c->n_scenes, cudaMemcpyHostToDevice, st));
   CREATE_CUDA(cudaMemsetAsync(c->d_v0, 0, vec, st));
   CREATE_CUDA(cudaMemsetAsync(c->d_v1, 0, vec, st));

@@ -1944,43 +1944,6 @@ __global__ void k_scatter_blocks(int N, const int32_t* __restrict__ row_ptr,
   }
 }
 
-// ---- scheduling of batched scenes ----
-
-constexpr int kOrderMax = 16384;   // scenes the one-CTA sort below handles
-
-// Longest-processing-time-first order for the next solve: scenes sorted by
-// the last solve's cost (sweeps x sliced-ELL entries) descending, ties by
-// index, with one CTA's bitonic sort over a power-of-two padded key array in
-// shared memory.  Only which CTA solves which scene changes.
-static __global__ void k_order_by_cost(int n, int p2, const int32_t* __restrict__ iters,
-                                       const int64_t* __restrict__ entries,
-                                       int32_t* __restrict__ order) {
-  extern __shared__ unsigned long long key[];
-  for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-    if (i < n) {
-      const unsigned long long cost =
-          min((unsigned long long)max(iters[i], 1) * (unsigned long long)entries[i], 0xffffffffull);
-      key[i] = ((0xffffffffull - cost) << 32) | (unsigned)i;
-    } else {
-      key[i] = ~0ull;
-    }
-  }
-  __syncthreads();
-  for (int k = 2; k <= p2; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-        const int m = i ^ j;
-        if (m > i) {
-          const unsigned long long a = key[i], b = key[m];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { key[i] = b; key[m] = a; }
-        }
-      }
-      __syncthreads();
-    }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int32_t)(key[i] & 0xffffffffull);
-}
-
 // ---- relative stop test of the adjoint: theta_th * ||b|| per scene ----
 // (b = dL/dv there; computed before the solve so that the solve kernels
 // carry nothing but one load for it)

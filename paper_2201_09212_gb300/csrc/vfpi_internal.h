@@ -85,7 +85,6 @@ struct vfpi_ctx {
   void *d_lam = nullptr, *d_lam_star = nullptr;
   void* d_dstar = nullptr;                  // D-contact v* staging [2 n_c]
   int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
-  int64_t* d_scene_entries = nullptr;       // sliced-ELL entries per scene (scheduling cost)
   double* d_norm_scale = nullptr;
   double* d_partials = nullptr;
   double* d_bbpart = nullptr;               // BB dot-product partials [2][max_grid][3]

@@ -457,21 +457,7 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   }
   if (e != cudaSuccess) return e;
   c->timed = true;
-  if ((e = cudaEventRecordWithFlags(c->ev1, s, flags)) != cudaSuccess) return e;
-  // batched scenes: the next solve pops them longest-processing-time first
-  // by this solve's cost (after the timed region)
-  if (c->path == 2 && c->n_scenes > 1 && c->n_scenes <= kOrderMax && !adjoint) {
-    int p2 = 1;
-    while (p2 < c->n_scenes) p2 <<= 1;
-    const size_t sm = 8 * (size_t)p2;
-    if (sm > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_order_by_cost, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-            cudaSuccess)
-      return e;
-    k_order_by_cost<<<1, 1024, sm, s>>>(c->n_scenes, p2, c->d_iters, c->d_scene_entries, c->d_order);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return cudaEventRecordWithFlags(c->ev1, s, flags);
 }
 
 }  // namespace vfpi
