@@ -192,3 +192,15 @@ def test_batched_tuner_times_whole_solves_and_restores_the_warm_start(uneven, tm
         assert np.array_equal(s.get_velocity(), batch.v0)      # warm start put back
         r = s.solve(batch.v0)
     assert np.array_equal(r.iters, ref.iters) and np.array_equal(r.v, ref.v)
+
+
+def test_cluster_shapes_f64():
+    """The FP64 instantiations (two 16-byte st.async pushes per row on the
+    shared-memory exchange path) give the CTA-per-scene kernel's iterates."""
+    lat = scenes.batched_lattices(12, seed=1357, side_range=(4, 11), dtype=np.float64)
+    batch = scenes.concat_scenes(lat)
+    ref, _ = run(batch, 0, 256, theta=1e-10, l_max=2000)
+    for var in (16, 19, 23, 25):
+        r, _ = run(batch, var, theta=1e-10, l_max=2000)
+        assert np.array_equal(r.iters, ref.iters), var
+        assert np.array_equal(r.v, ref.v) and np.array_equal(r.lam, ref.lam), var

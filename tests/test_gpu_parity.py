@@ -377,3 +377,15 @@ def test_tuner_picks_and_applies_a_shape(tmp_path):
         assert again["cached"] and again["kernel_variant"] == res["kernel_variant"]
         r = s.solve(sc.v0)
         assert np.isfinite(r.v).all()
+
+
+def test_tma_and_register_shapes_agree_in_f64():
+    sc = scenes.terrain_lattice(np.float64, dims=(40, 36, 6))
+    ref = None
+    with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=12, force_path=1, dtype="f64") as s:
+        for var in (0, 7, 8, 9, 10, 11, 12):
+            s.configure_launch(var, 0, 0)
+            r = s.solve(sc.v0)
+            if ref is None:
+                ref = (r.v.copy(), r.lam.copy())
+            assert np.array_equal(r.v, ref[0]) and np.array_equal(r.lam, ref[1]), var
