@@ -919,9 +919,15 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     double* part = ctl.partials + (l & 1) * gridDim.x;
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
     if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
-    double s2 = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += part[q];
-    s2 = block_allreduce<NT>(s2, red);
+    // one warp sums the CTA partials (fixed order) and broadcasts the total
+    if (threadIdx.x < 32) {
+      double s2w = 0.0;
+      for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s2w += part[q];
+      s2w = warp_sum(s2w);
+      if (threadIdx.x == 0) red[32] = s2w;
+    }
+    __syncthreads();
+    const double s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
@@ -1169,9 +1175,15 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     double* part = ctl.partials + (l & 1) * gridDim.x;
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
     if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
-    double s2 = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += NT) s2 += part[q];
-    s2 = block_allreduce<NT>(s2, red);
+    // one warp sums the CTA partials (fixed order) and broadcasts the total
+    if (threadIdx.x < 32) {
+      double s2w = 0.0;
+      for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s2w += part[q];
+      s2w = warp_sum(s2w);
+      if (threadIdx.x == 0) red[32] = s2w;
+    }
+    __syncthreads();
+    const double s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
