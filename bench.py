@@ -42,7 +42,7 @@ BATCH_CHEBYSHEV = (5, 1.0)   # Alg. 3 for the batched env steps' second figure
 ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
 ADJ_L_MAX = 5000
 ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
-NCU_TRAFFIC = {("58e641c9eac8ebcb", 7): 553356876}   # (source hash, launch shape): profiles/k_solve_grid_terrain_lattice_128x128x32.md
+NCU_TRAFFIC = {("cfbbb51e8da6d7d0", 0): 554110179}   # (source hash, launch shape): profiles/k_solve_grid_terrain_lattice_128x128x32.md
 
 
 def source_hash() -> str:
@@ -454,6 +454,8 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=64)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--grid-variant", type=int, default=None,
+                    help="fix the single scene's launch shape instead of tuning it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -479,7 +481,12 @@ def main():
     stream = torch.cuda.Stream()
     s = vfpi.Solver.from_scene(sc, theta_th=THETA_TH, l_max=L_MAX, norm="rms", stream=stream)
     s.set_velocity(torch.from_numpy(sc.v0).to(torch.device("cuda", local)))
-    tuned = tune.tune(s, sweeps=30, reps=3)      # launch shape (cached per layout and GPU)
+    if args.grid_variant is not None:            # a fixed launch shape (reproducible captures)
+        s.configure_launch(args.grid_variant, 0, 0)
+        tuned = {"kernel_variant": args.grid_variant, "block_threads": 0, "grid_ctas": 0,
+                 "ms_per_sweep": None, "cached": False}
+    else:
+        tuned = tune.tune(s, sweeps=30, reps=3)  # launch shape (cached per layout and GPU)
     lay = s.layout()
     dev = torch.device("cuda", local)
     v0 = torch.from_numpy(sc.v0).to(dev)
