@@ -722,7 +722,10 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
       return fail(VFPI_ERR_INVALID_ARG);
     }
   }
+  // kernel path (the grid path keeps A in symmetric storage as well, built by set_values)
   c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
+  if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
+  if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_ST(set_values(c, drow, dcol, A->vals, true, off_vals));
   // contacts, b, W
   CREATE_ST(set_contacts(c, Jc));
@@ -739,11 +742,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   }
   CREATE_ST(set_w(c));
 
-  // kernel path and launch shape
-  c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
+  // launch shape
   c->opts.grid_ctas = o->grid_ctas;
-  if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
-  if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   if (!apply_variant(c, o->kernel_variant, o->block_threads)) {
     c->err = "unknown kernel_variant for this path";
     return fail(VFPI_ERR_INVALID_ARG);

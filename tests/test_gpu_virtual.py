@@ -55,3 +55,34 @@ def test_virtual_node_ladder_and_converged_f64(make, path):
     ref = ov.solve(P, w, sc.v0, theta_th=1e-13, l_max=2_000_000)
     assert r.converged and abs(r.iters - ref.iters) <= 2
     assert np.abs(r.v - ref.v).max() <= 1e-9 * np.abs(ref.v).max()
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_paper_box_rollout_f64(path):
+    """The sliding box of Sec. V.B through the CUDA path in FP64 (k_v = 1 in
+    the harness's units), ten time steps: each step's velocities and normal
+    impulses are the oracle's V-FPI rollout's, the y error is mu times the z
+    error, and the sinking is -h (sum of the normal impulses) / (4 k_v), the
+    virtual-node perturbation of Sec. III.A."""
+    from tests.test_virtual_nodes import PAPER_BOX, box_rollout
+
+    def gpu(sc):
+        with vfpi.Solver.from_scene(sc, theta_th=1e-12, l_max=3_000_000, force_path=path) as s:
+            r = s.solve(sc.v0)
+        assert r.converged
+        return r.v, r.lam
+
+    def cpu(sc):
+        P = oracle_problem(sc)
+        r = ov.solve(P, ov.frobenius_w(P), sc.v0, theta_th=1e-12, l_max=3_000_000)
+        assert r.converged
+        return r.v, r.lam
+
+    k_v, mu, h = 1.0, PAPER_BOX["mu"], PAPER_BOX["h"]
+    ex, ey, ez, lam_n = box_rollout(k_v, gpu, steps=10)
+    rx, ry, rz, rlam = box_rollout(k_v, cpu, steps=10)
+    assert ex.max() <= 1e-12
+    assert np.allclose(ey, ry, rtol=1e-5, atol=0.0) and np.allclose(ez, rz, rtol=1e-5, atol=0.0)
+    assert np.allclose(lam_n, rlam, rtol=1e-5, atol=0.0)
+    assert np.allclose(ey / ez, mu, rtol=1e-5, atol=0.0)
+    assert np.allclose(ez, h * lam_n / (4 * k_v), rtol=1e-5, atol=0.0)

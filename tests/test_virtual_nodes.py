@@ -1,5 +1,7 @@
 """Virtual nodes (Sec. III.A, eq. vforce, eq. vnode): Prop. 1, Prop. 2 and an
 analytic sliding box, on the FP64 oracle."""
+import pathlib
+
 import numpy as np
 import pytest
 
@@ -155,3 +157,86 @@ def test_sliding_box_matches_the_analytic_motion():
     assert 5 < pen[0] / pen[1] < 20 and 5 < pen[1] / pen[2] < 20
     assert verr[0] > verr[1] > verr[2] and verr[1] / verr[2] > 5
     assert verr[2] < 0.05 * (steps * h * (F / m - mu * g))
+
+
+GOLDEN_BOX = pathlib.Path(__file__).parent / "golden" / "box_sliding_errors.txt"
+PAPER_BOX = dict(m=0.5, side=0.2, mu=0.2, h=0.01)
+
+
+def paper_box(k_v, v, z, F=2.0):
+    """The sliding box of Sec. V.B: a cube of side 0.2 m and mass 0.5 kg on
+    z = 0, friction coefficient 0.2, contacts at the four bottom vertices
+    through virtual nodes, a constant force F along y, time step 10 ms.  The
+    paper does not print its force; 2 N exceeds the friction limit
+    (0.98 N), so the box slides from the first step.  ``z`` is the current
+    height of the centre (its sinking), which sets the gap phi = z / h."""
+    m, L, mu, h = PAPER_BOX["m"], PAPER_BOX["side"], PAPER_BOX["mu"], PAPER_BOX["h"]
+    body = scenes.rigid_boxes([dict(m=m, size=(L, L, L), v=v, force=(0.0, F, 0.0))], h=h)
+    corners = [np.array([ax * L / 2, ay * L / 2, -L / 2]) for ax in (-1, 1) for ay in (-1, 1)]
+    jv = []
+    for p, r in enumerate(corners):
+        jv += [(p, i, B) for (_, i, B) in scenes.point_jacobian(0, r)]
+    R = scenes.contact_frames(np.tile(E_Z, (4, 1)))
+    return scenes.add_virtual_nodes(body, jv, 4, k_v, (np.arange(2, 6), -np.ones(4, int), R,
+                                                       np.full(4, mu), np.full(4, z / h)))
+
+
+def pgs_box_solve(sc):
+    """The augmented contact problem (eq. vnode) solved through its Delassus
+    operator: contacts act on the virtual nodes (J_c rows R_m at node 2 + m)."""
+    A = sc.dense_A()
+    J = np.zeros((3 * sc.n_c, A.shape[0]))
+    for q in range(sc.n_c):
+        J[3 * q:3 * q + 3, 3 * sc.node_i[q]:3 * sc.node_i[q] + 3] = sc.R[q]
+    v, lam = pgs_general(A, sc.b, J, sc.mu, sc.phi)
+    return v, lam.reshape(-1, 3)
+
+
+def box_rollout(k_v, solve, steps, F=2.0):
+    """Per-step position errors against the analytic motion (backward Euler of
+    a = F/m - mu g along y, no motion along x or z) and the summed normal
+    impulse of the four contacts."""
+    m, mu, h, g = PAPER_BOX["m"], PAPER_BOX["mu"], PAPER_BOX["h"], scenes.GRAVITY
+    v = np.zeros(6)
+    pos = np.zeros(3)
+    va = ya = 0.0
+    ex, ey, ez, lam_n = [], [], [], []
+    for _ in range(steps):
+        v, lam = solve(paper_box(k_v, v, pos[2], F))
+        v = np.asarray(v, float)[:6]
+        pos = pos + h * v[:3]
+        va += h * (F / m - mu * g)
+        ya += h * va
+        ex.append(abs(pos[0]))
+        ey.append(abs(pos[1] - ya))
+        ez.append(abs(pos[2]))
+        lam_n.append(float(np.asarray(lam, float).reshape(-1, 3)[:, 0].sum()))
+    return np.array(ex), np.array(ey), np.array(ez), np.array(lam_n)
+
+
+def test_paper_box_table_trend_on_the_oracle():
+    """The paper's table (tests/golden/box_sliding_errors.txt) shows, to its
+    printed rounding, no error along x, a y error of mu times the z error and
+    errors falling tenfold per decade of k_v.  The oracle's box shows the same,
+    and its sinking is the virtual-node perturbation of Sec. III.A: the SCC
+    hold on the virtual nodes, whose velocity differs from the contact point's
+    by k_v^-1 lambda, so with all four corners in contact
+    z_k = -h (sum of the normal impulses) / (4 k_v) at every step."""
+    rows = np.loadtxt(GOLDEN_BOX)
+    half = 0.5e-4                                     # four printed decimals
+    mu = PAPER_BOX["mu"]
+    for k_v, exm, eym, ezm in rows:
+        assert exm == 0.0
+        assert (eym - half) / (ezm + half) <= mu <= (eym + half) / (ezm - half), k_v
+    for (k0, _, _, z0), (k1, _, _, z1) in zip(rows[:-1], rows[1:]):
+        assert k1 == 10 * k0
+        assert abs(z0 / z1 - 10.0) <= 0.01 * 10.0 + 10.0 * half * (1 / z1 + 1 / z0)
+    h = PAPER_BOX["h"]
+    means = []
+    for k_v in (1.0, 10.0):                           # the harness's k_v (A in impulse units)
+        ex, ey, ez, lam_n = box_rollout(k_v, pgs_box_solve, steps=20)
+        assert ex.max() <= 1e-15
+        assert np.allclose(ey / ez, mu, rtol=1e-7, atol=0.0)
+        assert np.allclose(ez, h * lam_n / (4 * k_v), rtol=1e-9, atol=0.0)
+        means.append(ez.mean())
+    assert abs(means[0] / means[1] - 10.0) <= 0.01 * 10.0
