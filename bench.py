@@ -36,13 +36,15 @@ THETA_TH = 1e-6          # RMS residual threshold (m/s per DOF)
 L_MAX = 200
 FALLBACK_HBM_GBS = 6800.0
 
-# ncu DRAM traffic (read + write bytes per sweep) of the solve kernel, keyed by
-# the hash of the CUDA sources it was captured from; stale entries read as null.
 BATCH_CHEBYSHEV = (5, 1.0)   # Alg. 3 for the batched env steps' second figure
 ADJ_THETA_REL = 1e-4        # adjoint stop: ||u^{l+1} - u^l|| < 1e-4 ||dL/dv|| (rms, per scene)
 ADJ_L_MAX = 5000
 ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under-relaxation)
-NCU_TRAFFIC = {("cfbbb51e8da6d7d0", 0): 554110179, ("cfbbb51e8da6d7d0", 7): 553515078}   # (source hash, launch shape): profiles/k_solve_grid_terrain_lattice_128x128x32.md
+# ncu DRAM traffic (read + write bytes per sweep) of the single-scene solve
+# kernel, keyed by (hash of the CUDA sources it was captured from, kernel
+# variant), each captured at the variant's default CTA count; stale entries
+# read as null (profiles/k_solve_grid_terrain_lattice_128x128x32.md)
+NCU_TRAFFIC = {("30b2c5814acd1015", 0): 554449911, ("30b2c5814acd1015", 7): 553640967}
 
 
 def source_hash() -> str:
