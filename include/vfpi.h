@@ -112,7 +112,10 @@ typedef struct {
   int32_t n_scenes;        /* 0 or 1: one problem; > 1: independent scenes          */
   const int32_t* scene_ptr;/* [n_scenes+1] node offsets of the scenes (batched)     */
   int32_t block_threads;   /* 0 = default; threads per CTA of the solve kernel       */
-  int32_t force_path;      /* 0 = auto, 1 = grid-wide kernel, 2 = CTA-per-scene      */
+  int32_t force_path;      /* 0 = auto: CTA-per-scene (2) for several scenes or a
+                              scene of at most 64 slices (2,048 nodes), else
+                              grid-wide (1); 1 or 2 forces that path; other
+                              values: VFPI_ERR_INVALID_ARG                     */
   int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..15 (threads per
                               CTA, CTAs/SM register budget, prefetch, TMA ring,
                               symmetric storage); scene path 0 or
@@ -156,7 +159,7 @@ enum {
   VFPI_VARIANT_SYM_256_3 = 13,
   VFPI_VARIANT_SYM_256_4 = 14,
   VFPI_VARIANT_SYM_512_1 = 15,
-  /* Scene path (n_scenes > 1 or force_path 2): shared-memory-resident
+  /* Scene path (see force_path): shared-memory-resident
    * cluster kernel.  Each CTA copies its share of a scene's matrix into shared
    * memory once per solve (1-D bulk copies) and every sweep reads it there; a
    * scene larger than one CTA's share is split over the CTAs of a
