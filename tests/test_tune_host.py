@@ -1,0 +1,147 @@
+"""Host logic of the launch-shape autotuner (CPU, fake solver): the persistent
+grid sizes it tries, the margin a special kernel must win by, shapes the GPU
+refuses, the cache, and that tuning leaves the solver's tolerance and warm
+start as it found them."""
+import json
+import math
+
+import numpy as np
+import pytest
+
+from paper_2201_09212_gb300 import tune
+
+
+class FakeSolver:
+    """The calls tune() makes, with a kernel time given by cost(variant,
+    block_threads, grid_ctas) per launch."""
+
+    def __init__(self, path, cost, refuse=(), n_slices=16384, max_grid=456, sms=152):
+        self.path, self.cost, self.refuse = path, cost, set(refuse)
+        self.n_slices, self.max_grid, self.sms = n_slices, max_grid, sms
+        self._theta_th, self._l_max = 1e-6, 200
+        self.tol = (self._theta_th, self._l_max)
+        self.n_scenes = 1 if path == 1 else 64
+        self.np_dtype = np.float32
+        self.shape = (0, 0, 0)
+        self.v = np.arange(6, dtype=np.float32)
+        self.launches = 0
+        self.tol_at_launch = []
+
+    def layout(self):
+        return dict(path=self.path, n_slices=self.n_slices, slots=7, max_grid=self.max_grid,
+                    sms=self.sms, grid=self.shape[2] or self.max_grid)
+
+    def configure_launch(self, var, bt, grid):
+        if var in self.refuse:
+            raise RuntimeError("shape not available")
+        self.shape = (var, bt, grid)
+
+    def set_tolerance(self, theta, l_max):
+        self.tol = (theta, l_max)
+
+    def solve_async(self):
+        self.launches += 1
+        self.tol_at_launch.append(self.tol)
+        self.v = self.v + 1.0            # a solve moves the iterate
+
+    def status(self):
+        return np.array([20, 17]), None, None
+
+    def last_kernel_ms(self):
+        return self.cost(*self.shape)
+
+    def get_velocity(self):
+        return self.v.copy()
+
+    def set_velocity(self, v):
+        self.v = np.array(v, dtype=np.float32)
+
+
+@pytest.fixture(autouse=True)
+def fake_gpu_name(monkeypatch):
+    import torch
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "FakeGPU")
+
+
+@pytest.mark.parametrize("n,w,mx,sms", [(16384, 8, 456, 152), (2245, 8, 304, 152), (7, 2, 608, 152),
+                                        (100000, 16, 152, 152), (5000, 4, 1216, 152)])
+def test_grid_candidates(n, w, mx, sms):
+    cand = tune._grid_candidates(n, w, mx, sms)
+    assert 0 in cand and all(0 < g <= mx for g in cand if g)
+    # the fewest CTAs that keep the full grid's slices per warp
+    k = math.ceil(n / (mx * w))
+    g = min(mx, math.ceil(n / (w * k)))
+    assert g in cand
+    assert math.ceil(n / (g * w)) <= k
+    if g > 1:
+        assert math.ceil(n / ((g - 1) * w)) > k or g == mx
+    # SM-count multiples up to the CTAs that still have work
+    need = math.ceil(n / w)
+    for r in range(1, mx // sms + 1):
+        assert min(need, r * sms) in cand
+
+
+def grid_cost(special_factor):
+    def cost(var, bt, grid):
+        base = 1.0 + 0.001 * var + (0.0 if grid == 410 else 0.01)
+        return base * (special_factor if var >= 8 else 1.0)
+    return cost
+
+
+def test_special_kernel_needs_the_margin(tmp_path):
+    # the TMA ring (8) is 1 % faster than the best plain shape: inside the margin
+    s = FakeSolver(1, grid_cost(0.99 / 1.008), refuse=range(12, 16))
+    r = tune.tune(s, sweeps=10, reps=1, cache=None)
+    assert (r["kernel_variant"], r["grid_ctas"]) == (0, 410)
+    assert s.shape == (0, 0, 410)
+    # 5 % faster: taken
+    s = FakeSolver(1, grid_cost(0.95 / 1.008), refuse=range(12, 16))
+    r = tune.tune(s, sweeps=10, reps=1, cache=None)
+    assert r["kernel_variant"] == 8 and s.shape[0] == 8
+
+
+def test_refused_shapes_are_skipped_and_tolerance_restored():
+    s = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16))
+    r = tune.tune(s, sweeps=10, reps=2, cache=None)
+    tried = {t["kernel_variant"] for t in r["trials"]}
+    assert tried == set(range(12)) and s.tol == (1e-6, 200)
+    assert set(s.tol_at_launch) == {(-1.0, 10)}          # fixed sweep count, no stop test
+    assert all(t["ms_per_sweep"] == pytest.approx(grid_cost(1.0)(t["kernel_variant"], 0,
+                                                                   t["grid_ctas"]) / 10)
+               for t in r["trials"])
+
+
+def test_cache_round_trip(tmp_path):
+    cache = str(tmp_path / "sub" / "tune.json")
+    s = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16))
+    r = tune.tune(s, sweeps=10, reps=1, cache=cache)
+    assert not r["cached"]
+    with open(cache) as f:
+        table = json.load(f)
+    assert len(table) == 1 and next(iter(table.values()))["kernel_variant"] == r["kernel_variant"]
+    s2 = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16))
+    r2 = tune.tune(s2, sweeps=10, reps=1, cache=cache)
+    assert r2["cached"] and s2.launches == 0
+    assert s2.shape == (r["kernel_variant"], r["block_threads"], r["grid_ctas"])
+    # another layout is another entry
+    s3 = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16), n_slices=2245)
+    assert not tune.tune(s3, sweeps=10, reps=1, cache=cache)["cached"]
+    with open(cache) as f:
+        assert len(json.load(f)) == 2
+    assert not list((tmp_path / "sub").glob("*.tmp"))
+
+
+def test_scene_path_times_whole_solves_and_restores_the_warm_start():
+    def cost(var, bt, grid):           # whole-solve times: cluster shapes 2.98 ms
+        return 2.98 if var >= 16 else {64: 5.0, 128: 4.0, 256: 3.0, 512: 3.5}[bt]
+    s = FakeSolver(2, cost, refuse=range(20, 26))
+    v_start = s.get_velocity()
+    r = tune.tune(s, sweeps=10, reps=2, cache=None)
+    shapes = {(t["kernel_variant"], t["block_threads"]) for t in r["trials"]}
+    assert shapes == {(0, 64), (0, 128), (0, 256), (0, 512)} | {(v, 0) for v in range(16, 20)}
+    # every trial starts from the same warm start and is timed at the solver's tolerance
+    assert all(t["ms_per_solve"] == pytest.approx(t["ms_per_sweep"] * 20) for t in r["trials"])
+    assert set(s.tol_at_launch) == {(1e-6, 200)}
+    # cluster shapes at 2.98 ms are inside the 2 % margin of 3.0 ms: the plain 256
+    assert (r["kernel_variant"], r["block_threads"]) == (0, 256)
+    assert np.array_equal(s.get_velocity(), v_start) and s.tol == (1e-6, 200)
