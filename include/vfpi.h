@@ -124,7 +124,9 @@ typedef struct {
   int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
                               fit, capped at one warp per 32-row slice)              */
   int32_t chebyshev_ls;    /* Chebyshev acceleration (Alg. 3): slow-start index
-                              l_s >= 3, or 0 for the plain iteration of Alg. 1     */
+                              l_s >= 4 (the estimate rho of eq. varrho first
+                              exists after iteration 3), or 0 for the plain
+                              iteration of Alg. 1                                 */
   double chebyshev_u;      /* Alg. 3 under-relaxation u in (0, 1] (1 = the printed
                               update of eq. chebyup)                               */
   int32_t reserved[2];
@@ -308,7 +310,9 @@ vfpi_status vfpi_set_barzilai_borwein(vfpi_t ctx, int32_t rule, double alpha0);
  * nu = 1 before the slow start l_s, 2 / (2 - rho^2) at l_s, then
  * 4 / (4 - rho^2 nu); v^{l+1} = nu (u (v** - v^l) + v^l - v^{l-1}) + v^{l-1}
  * with v** the V-FPI step and rho = min(||v^l - v^{l-1}|| / ||v^{l-1} - v^{l-2}||, 1).
- * l_s = 0 switches it off; else l_s >= 3 and 0 < u <= 1.  The fixed point,
+ * rho is computed after the stop test of iteration l >= 3 and used from
+ * iteration 4 on, so l_s = 0 switches it off, else l_s >= 4 and 0 < u <= 1
+ * (VFPI_ERR_INVALID_ARG otherwise).  The fixed point,
  * W and the adjoint are unchanged. */
 vfpi_status vfpi_set_chebyshev(vfpi_t ctx, int32_t l_s, double u);
 
@@ -316,7 +320,7 @@ vfpi_status vfpi_set_chebyshev(vfpi_t ctx, int32_t l_s, double u);
  * apart from the forward solve's: the adjoint iteration is linear at the
  * frozen active set and has the spectrum of the forward iteration's
  * linearisation, so the semi-iteration applies to it as it stands.  l_s = 0
- * (the default) switches it off; else l_s >= 3 and 0 < u <= 1.  The adjoint's
+ * (the default) switches it off; else l_s >= 4 and 0 < u <= 1.  The adjoint's
  * fixed point is unchanged.  There is no counterpart in the paper, which does
  * not differentiate the solve. */
 vfpi_status vfpi_set_adjoint_chebyshev(vfpi_t ctx, int32_t l_s, double u);

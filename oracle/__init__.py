@@ -18,11 +18,17 @@ delassus   Projected Gauss-Seidel on the dense Delassus operator (eq. delassus),
 enumerate  Brute-force active-set enumeration for 1-3 contacts: every
            open/stick/slip assignment of the Signorini-Coulomb conditions
            (eq. scc) solved directly.
-checks     Dynamics residual (eq. lindyn), Signorini-Coulomb residual (eq. scc).
+checks     Dynamics residual (eq. lindyn), Signorini-Coulomb residual (eq. scc),
+           open/stick/slip classification.
 adjoint    Dense implicit-function adjoint of the converged fixed point
            (the map f(v) of Sec. IV) at a frozen active set.
 
-Every function is pinned by the CPU tests against closed forms, invariants or
-brute force.  Functions without such a pin say "parity unpinned" in their
-docstring; at present there are none.
+Every function is pinned by the CPU tests against closed forms, invariants,
+brute force or hand-worked values (the residual checkers against contacts
+built to break exactly one condition of eq. (scc) each, with the violation
+worked out by hand), and planted mistakes in each are caught by those pins.
+Functions without such a pin say "parity unpinned" in their docstring; at
+present there are none.  Trajectories over many time steps are compared step
+by step only: their stick/slip switches make long rollouts sensitive to
+rounding, so no rollout-level pin exists.
 """

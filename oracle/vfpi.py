@@ -286,10 +286,11 @@ def solve_chebyshev(P: Problem, w: np.ndarray, v0: np.ndarray, theta_th: float, 
     the under-relaxation ``u`` of the text; ``u = 1`` is the printed update),
     ``theta = ||v^{l+1} - v^l||``, and after the stop test
     ``rho = min(||v^l - v^{l-1}|| / ||v^{l-1} - v^{l-2}||, 1)`` (eq. varrho, taken
-    with the current l).  Needs ``l_s >= 3`` so that rho exists when first used;
-    ``rho_fixed`` replaces the estimate by a given spectral radius (then
-    ``l_s >= 2``)."""
-    if l_s < (2 if rho_fixed is not None else 3):
+    with the current l).  The loop starts from ``v^1`` (the warm start), so
+    that ratio first exists after the stop test of ``l = 3`` and is first used
+    by the weight of ``l = 4``: hence ``l_s >= 4``.  ``rho_fixed`` replaces the
+    estimate by a given spectral radius (then ``l_s >= 2``)."""
+    if l_s < (2 if rho_fixed is not None else 4):
         raise ValueError("l_s too small")
     v = np.asarray(v0, dtype=np.float64).copy()
     v_prev = v.copy()

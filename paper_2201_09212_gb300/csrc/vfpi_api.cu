@@ -545,8 +545,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   if (o->block_threads && o->block_threads != 64 && o->block_threads != 128 &&
       o->block_threads != 256 && o->block_threads != 512)
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
-  if (o->chebyshev_ls != 0 && (o->chebyshev_ls < 3 || !(o->chebyshev_u > 0 && o->chebyshev_u <= 1)))
-    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  if (o->chebyshev_ls != 0 && (o->chebyshev_ls < 4 || !(o->chebyshev_u > 0 && o->chebyshev_u <= 1)))
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
 
   vfpi_ctx* c = new (std::nothrow) vfpi_ctx;
   if (!c) return arg_fail(nullptr, VFPI_ERR_OOM, "host allocation failed");
@@ -1142,8 +1142,8 @@ vfpi_status vfpi_set_barzilai_borwein(vfpi_t c, int32_t rule, double alpha0) {
 
 vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
-  if (l_s != 0 && (l_s < 3 || !(u > 0 && u <= 1)))
-    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  if (l_s != 0 && (l_s < 4 || !(u > 0 && u <= 1)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
   if (l_s && c->bb_rule)
     return arg_fail(c, VFPI_ERR_UNSUPPORTED, "Barzilai-Borwein steps and Chebyshev acceleration exclude each other");
   c->opts.chebyshev_ls = l_s;
@@ -1153,8 +1153,8 @@ vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
 
 vfpi_status vfpi_set_adjoint_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
-  if (l_s != 0 && (l_s < 3 || !(u > 0 && u <= 1)))
-    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 3 and 0 < u <= 1");
+  if (l_s != 0 && (l_s < 4 || !(u > 0 && u <= 1)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
   c->adj_cheb_ls = l_s;
   c->adj_cheb_u = u;
   return VFPI_OK;

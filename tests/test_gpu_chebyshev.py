@@ -21,7 +21,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("path", [1, 2])
-@pytest.mark.parametrize("l_s,u", [(5, 0.9), (3, 1.0)])
+@pytest.mark.parametrize("l_s,u", [(5, 0.9), (4, 1.0)])
 def test_ladder_f64_matches_oracle_alg3(path, l_s, u):
     rng = np.random.default_rng(21)
     sc = scenes.random_problem(rng, 60, 10, d_contacts=4, density=0.08, couple=0.4)
@@ -84,6 +84,8 @@ def test_invalid_chebyshev_settings_are_rejected():
     sc = scenes.small_lattice(np.float64)
     with pytest.raises(vfpi.VfpiError):
         vfpi.Solver.from_scene(sc, chebyshev_ls=2)
+    with pytest.raises(vfpi.VfpiError):
+        vfpi.Solver.from_scene(sc, chebyshev_ls=3)   # eq. varrho has no value yet at l = 3
     with vfpi.Solver.from_scene(sc) as s:
         with pytest.raises(vfpi.VfpiError):
             s.set_chebyshev(5, 1.5)

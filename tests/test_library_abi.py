@@ -86,7 +86,7 @@ def test_host_only_entry_points(L):
     assert L.vfpi_create(C.byref(bsr), C.c_void_p(1), None, C.c_double(1e-3), C.byref(o), None,
                          C.byref(h)) == -1
     o.operator_ = 0
-    o.chebyshev_ls = 2
+    o.chebyshev_ls = 3
     assert L.vfpi_create(C.byref(bsr), C.c_void_p(1), None, C.c_double(1e-3), C.byref(o), None,
                          C.byref(h)) == -1
     assert L.vfpi_step(None, None) == -1

@@ -15,11 +15,13 @@ import pytest
 
 import oracle.vfpi as ov
 import oracle.adjoint as oadj
+import oracle.checks as ochk
 import oracle.delassus as odel
 from tests import test_oracle_chebyshev as cheb
 from tests import test_oracle_proximal as prox
 from tests import test_oracle_bb as bbt
 from tests import test_oracle_anisotropic as ani
+from tests import test_oracle_checks as chk
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -58,6 +60,31 @@ MUTANTS = {
                      "return 4.0 / (4.0 - rho * nu_prev)"),
     "cheby_anchor": (ov, "solve_chebyshev", "v_next = nu * (u * (r.v_next - v) + v - v_prev) + v_prev",
                      "v_next = nu * (u * (r.v_next - v) + v - v_prev) + v"),
+    "cheby_rho_latest": (ov, "solve_chebyshev",
+                         "rho = min(thetas[l - 2] / thetas[l - 3], 1.0) if thetas[l - 3] > 0 else 1.0",
+                         "rho = min(thetas[l - 1] / thetas[l - 2], 1.0) if thetas[l - 2] > 0 else 1.0"),
+    "cheby_ls_three": (ov, "solve_chebyshev", "if l_s < (2 if rho_fixed is not None else 4):",
+                       "if l_s < (2 if rho_fixed is not None else 3):"),
+    "scc_zero": (ochk, "scc_terms", "return np.stack([t1, t2, t3, t4], axis=1)",
+                 "return np.zeros((u.shape[0], 4))"),
+    "scc_drop_normal": (ochk, "scc_terms", "np.stack([t1, t2, t3, t4], axis=1)",
+                        "np.stack([0 * t1, t2, t3, t4], axis=1)"),
+    "scc_drop_cone": (ochk, "scc_terms", "np.stack([t1, t2, t3, t4], axis=1)",
+                      "np.stack([t1, 0 * t2, t3, t4], axis=1)"),
+    "scc_drop_slip": (ochk, "scc_terms", "np.stack([t1, t2, t3, t4], axis=1)",
+                      "np.stack([t1, t2, 0 * t3, t4], axis=1)"),
+    "scc_drop_dissipation": (ochk, "scc_terms", "np.stack([t1, t2, t3, t4], axis=1)",
+                             "np.stack([t1, t2, t3, 0 * t4], axis=1)"),
+    "scc_dissipation_sign": (ochk, "scc_terms", "ut[:, None] * lam[:, 1:] + lt[:, None] * u[:, 1:]",
+                             "ut[:, None] * lam[:, 1:] - lt[:, None] * u[:, 1:]"),
+    "scc_residual_min": (ochk, "scc_residual", "scc_terms(u, lam, P.mu, v_scale).max()",
+                         "scc_terms(u, lam, P.mu, v_scale).min()"),
+    "scc_no_gap": (ochk, "contact_velocity", "u[:, 0] += P.phi", "u[:, 0] += 0.0 * P.phi"),
+    "dynamics_no_contact": (ochk, "dynamics_residual", "- P.Jc.T @", "- 0.0 * P.Jc.T @"),
+    "mode_slip_flipped": (ochk, "mode_of", "(lt >= mu * lam[:, 0] * (1 - 1e-9))",
+                          "(lt <= mu * lam[:, 0] * (1 - 1e-9))"),
+    "mode_open_strict": (ochk, "mode_of", "np.where(lam[:, 0] <= rel * scale, 0, 1)",
+                         "np.where(lam[:, 0] < 0, 0, 1)"),
 }
 
 
@@ -90,13 +117,22 @@ def _pin_suite():
         lambda: bbt.test_bb_quotients_on_an_eigenvector(),
         lambda: bbt.test_without_contacts_bb_is_the_textbook_gradient_method(),
         lambda: ani.test_elliptic_projection_is_the_nearest_point(rng()),
+        lambda: cheb.test_rho_is_eq_varrho_with_the_current_l(4, 1.0),
+        lambda: cheb.test_rho_is_eq_varrho_with_the_current_l(6, 0.8),
+        lambda: cheb.test_slow_start_before_eq_varrho_exists_is_rejected(),
+        lambda: chk.test_scc_terms_flag_each_violation_in_its_column(),
+        lambda: chk.test_scc_residual_is_zero_on_valid_and_at_least_the_violation_on_each_case(),
+        lambda: chk.test_scc_residual_scales_with_the_gap_term(),
+        lambda: chk.test_contact_velocity_uses_the_frame_and_the_d_contact_sign(),
+        lambda: chk.test_dynamics_residual_hand_value(),
+        lambda: chk.test_mode_of_classifies_open_stick_slip(),
     ]
     for call in calls:
         try:
             with np.errstate(all="ignore"):
                 call()
         except (AssertionError, np.linalg.LinAlgError, ValueError, ArithmeticError,
-                IndexError):
+                IndexError, pytest.fail.Exception):
             return False
     return True
 
@@ -111,6 +147,7 @@ def test_pins_catch_planted_mistake(name, monkeypatch):
     monkeypatch.setattr(module, fname, ns[fname])
     monkeypatch.setattr(pins, fname, ns[fname], raising=False)
     monkeypatch.setattr(prox, fname, ns[fname], raising=False)
+    monkeypatch.setattr(cheb, fname, ns[fname], raising=False)
     if module is ov:
         # functions imported by name elsewhere in the oracle follow the mutant
         monkeypatch.setattr(oadj, fname, ns[fname], raising=False)
