@@ -235,6 +235,13 @@ vfpi_status vfpi_solve_async(vfpi_t ctx);
 /* Synchronise and read the last solve's iteration counts and residuals
  * (arrays of n_scenes entries in batched mode; nullable). */
 vfpi_status vfpi_get_status(vfpi_t ctx, int32_t* iters_out, double* theta_out);
+/* Synchronise and read, per scene, how the last solve or adjoint solve ended
+ * (Alg. 1's two exits, plus the failures): VFPI_OK (theta < theta_th),
+ * VFPI_NOT_CONVERGED (l = l_max reached first), VFPI_ERR_NONFINITE (a
+ * non-finite residual), VFPI_ERR_TIMEOUT (a bounded wait of the launch ran
+ * out; set for every scene).  status_out: host array of n_scenes entries
+ * (required).  Returns VFPI_OK unless the read itself fails. */
+vfpi_status vfpi_get_scene_status(vfpi_t ctx, int32_t* status_out);
 
 /* Adjoint of the converged fixed point v = f(v; b, phi, mu) of Sec. IV,
  * f(v) = v* + W J_c^T ProjectFC(lambda*(v*)), at the active set frozen by

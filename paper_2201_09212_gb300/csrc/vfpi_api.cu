@@ -955,6 +955,21 @@ vfpi_status vfpi_get_status(vfpi_t c, int32_t* iters_out, double* theta_out) {
   return worst;
 }
 
+vfpi_status vfpi_get_scene_status(vfpi_t c, int32_t* status_out) {
+  CTX_CHECK(c);
+  if (!status_out) return arg_fail(c, VFPI_ERR_INVALID_ARG, "status_out is required");
+  const int S = c->n_scenes;
+  std::vector<int32_t> stv(S);
+  int err = 0;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(stv.data(), c->d_status, 4 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  // a wait that ran out invalidates every scene of that launch
+  if (err & 1) std::fill(stv.begin(), stv.end(), (int32_t)VFPI_ERR_TIMEOUT);
+  std::memcpy(status_out, stv.data(), 4 * (size_t)S);
+  return VFPI_OK;
+}
+
 vfpi_status vfpi_solve_async(vfpi_t c) {
   CTX_CHECK(c);
   VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, false)));

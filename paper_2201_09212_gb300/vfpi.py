@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "VFPI_OK", 1: "VFPI_NOT_CONVERGED", -1: "VFPI_ERR_INVALID_ARG
                 -2: "VFPI_ERR_NONFINITE", -3: "VFPI_ERR_CUDA", -4: "VFPI_ERR_OOM",
                 -5: "VFPI_ERR_TIMEOUT", -6: "VFPI_ERR_CONTACT_OVERLAP",
                 -7: "VFPI_ERR_UNSUPPORTED"}
+STATUS_CODES = {name: code for code, name in STATUS_NAMES.items()}
 DTYPES = {"f32": (0, np.float32), "f64": (1, np.float64)}
 W_MODES = {"frobenius": 0, "scalar": 1, "user": 2}
 NORMS = {"abs": 0, "rms": 1}
@@ -29,6 +30,7 @@ OPERATORS = {"strict": 0, "proximal": 1}
 EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_velocity", "vfpi_get_velocity", "vfpi_get_lambda", "vfpi_get_w",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
+            "vfpi_get_scene_status",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
             "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
             "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
@@ -98,6 +100,7 @@ def lib():
         "vfpi_solve": (st, [vp, vp, vp, vp, vp]),
         "vfpi_solve_async": (st, [vp]),
         "vfpi_get_status": (st, [vp, vp, vp]),
+        "vfpi_get_scene_status": (st, [vp, vp]),
         "vfpi_integrate": (st, [vp, vp]),
         "vfpi_matvec": (st, [vp, vp, vp]),
         "vfpi_last_kernel_ms": (st, [vp, vp]),
@@ -290,6 +293,12 @@ class Solver:
         st = self._check(self._L.vfpi_get_status(self._h, iters.ctypes.data, theta.ctypes.data),
                          allow_nc=True)
         return iters, theta, st
+
+    def scene_status(self):
+        """Per-scene outcome of the last solve or adjoint solve (status codes)."""
+        out = np.zeros(self.n_scenes, dtype=np.int32)
+        self._check(self._L.vfpi_get_scene_status(self._h, out.ctypes.data))
+        return out
 
     def step(self) -> float:
         theta = np.zeros(max(self.n_scenes, 1), dtype=np.float64)

@@ -139,3 +139,36 @@ def test_checkpointing_does_not_change_the_gradient(scene):
     b = gpu_rollout(scene, "f32", checkpoint=0)
     assert a[0] == b[0]
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_autograd_solve_fails_loudly(scene):
+    """A divergent step size (W = alpha I far above 2 / sigma_max) makes the
+    forward residual non-finite: the differentiable solve raises VfpiError
+    instead of returning the iterate.  A solve that reaches l_max warns with
+    the scene indices (or raises on request), forward and adjoint alike."""
+    from paper_2201_09212_gb300 import autograd as ag
+    dev = torch.device("cuda")
+    sc = scene
+    H = LatticeHarness(sc, dev, dtype=torch.float64)
+    v0 = torch.as_tensor(sc.v0, dtype=torch.float64, device=dev)
+    mu = torch.as_tensor(sc.mu, dtype=torch.float64, device=dev).requires_grad_(True)
+    b = torch.as_tensor(sc.b, dtype=torch.float64, device=dev).requires_grad_(True)
+    phi = torch.as_tensor(sc.phi, dtype=torch.float64, device=dev)
+    with vfpi.Solver.from_scene(sc, dtype="f64", w_mode="scalar", alpha=1e6, theta_th=1e-12,
+                                l_max=3000) as s:
+        with pytest.raises(vfpi.VfpiError) as e:
+            ag.vfpi_solve(s, b, phi, mu, v0)
+        assert e.value.status == vfpi.STATUS_CODES["VFPI_ERR_NONFINITE"]
+    with vfpi.Solver.from_scene(sc, dtype="f64", theta_th=1e-14, l_max=3) as s:
+        with pytest.warns(ag.VfpiNotConvergedWarning, match=r"forward solve: 2 scene\(s\)"):
+            v = ag.vfpi_solve(s, b, phi, mu, v0)
+        assert s.not_converged["forward"].tolist() == [0, 1]
+        with pytest.raises(ag.VfpiNotConverged):
+            ag.vfpi_solve(s, b, phi, mu, v0, on_not_converged="raise")
+        s.set_tolerance(1e-13, 100000)
+        v = ag.vfpi_solve(s, b, phi, mu, v0)
+        assert s.not_converged["forward"].size == 0
+        s.set_adjoint_tolerance(1e-14, 2, relative=True)
+        with pytest.warns(ag.VfpiNotConvergedWarning, match=r"adjoint solve"):
+            H.com_z(H.x_rest + sc.h * v).sum().backward()
+        assert s.not_converged["adjoint"].tolist() == [0, 1]
