@@ -357,14 +357,19 @@ vfpi_status vfpi_set_adjoint_tolerance(vfpi_t ctx, double theta_th, int32_t l_ma
  *  - FP32 only.  A, b, the contact arrays, v_in, v_out and lambda_out
  *    (n_c * 3, caller's contact order) must be device memory; iters_out and
  *    theta_out are host scalars (nullable).  The call synchronises the stream
- *    to read them back.  Inputs are not re-validated beyond index ranges
- *    (vfpi_create's checks do not run); out-of-range indices give
- *    VFPI_ERR_INVALID_ARG.
+ *    to read them back.  On the device, before any block is read, the call
+ *    checks row_ptr (row_ptr[0] == 0, row_ptr[n_nodes] == A->nnzb, 1..n_nodes
+ *    blocks per row) and the node indices of the contacts, then the column
+ *    indices; a failure gives VFPI_ERR_INVALID_ARG.  A node claimed by two
+ *    contacts, or a D-contact joining a node to itself, gives
+ *    VFPI_ERR_CONTACT_OVERLAP.  Nothing else of vfpi_create's validation runs
+ *    (sorted columns, finite values, orthonormal frames, mu >= 0 are the
+ *    caller's to guarantee).  On any of these errors no output is written.
  *  - Limit: n_nodes <= VFPI_NOALLOC_MAX_NODES (4096, i.e. 12,288 DOF) and
  *    n_c <= n_nodes; larger problems are rejected with VFPI_ERR_INVALID_ARG.
- *  - Its scratch is a fixed array of about 0.4 MB in device memory, part of the
- *    library image: every GPU that loads the library holds it until the
- *    process exits.  The first call on a device looks up the array's device
+ *  - Its scratch is a fixed array of 68 * VFPI_NOALLOC_MAX_NODES + 64 =
+ *    278,592 bytes in device memory, part of the library image: every GPU
+ *    that loads the library holds it until the process exits.  The first call on a device looks up the array's device
  *    address (with that device current); make that first call before any
  *    stream capture.
  *  - All calls on a device share that one array, and it keeps the previous

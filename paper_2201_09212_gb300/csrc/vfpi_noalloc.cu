@@ -40,10 +40,17 @@ constexpr size_t kScratchBytes = kOffStatus + 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+static_assert(kScratchBytes == 68ull * kMaxNodes + 64, "scratch size stated in include/vfpi.h");
+
+// error bits set by the kernel's input checks
+constexpr int kErrIndex = 1;     // a node or column index out of range
+constexpr int kErrOverlap = 2;   // a node in two contacts, or a D-contact with i == j
+constexpr int kErrRowPtr = 4;    // row_ptr not 0 .. nnzb with 1..n_nodes blocks per row
+
 struct NoallocStatus {
   int32_t iters;
   int32_t status;
-  int32_t err;      // bit 0: index out of range
+  int32_t err;      // kErr* bits
   int32_t pad;
   double theta;
 };
@@ -85,7 +92,7 @@ __device__ __forceinline__ void one_shot(const float* R, float mu, float phi, fl
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_solve_noalloc(int N, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+k_solve_noalloc(int N, int nnzb, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                 const float* __restrict__ vals, const float* __restrict__ b, int n_c,
                 const int32_t* __restrict__ node_i, const int32_t* __restrict__ node_j,
                 const float* __restrict__ R, const float* __restrict__ mu,
@@ -107,20 +114,35 @@ k_solve_noalloc(int N, const int32_t* __restrict__ row_ptr, const int32_t* __res
     cslot[i] = -1;
     v0[i] = make_float4(v_in[3 * i], v_in[3 * i + 1], v_in[3 * i + 2], 0.f);
   }
-  __syncthreads();
-  for (int m = tid; m < n_c; m += kThreads) {
-    const int i = node_i[m], j = node_j ? node_j[m] : -1;
-    if (i < 0 || i >= N || j < -1 || j >= N) { atomicOr(&s_err, 1); continue; }
-    cslot[i] = m;
-    if (j >= 0) cslot[j] = m;
+  // row pointers first: every later loop over a row's blocks trusts them
+  if (tid == 0 && (row_ptr[0] != 0 || row_ptr[N] != nnzb)) atomicOr(&s_err, kErrRowPtr);
+  for (int i = tid; i < N; i += kThreads) {
+    const int len = row_ptr[i + 1] - row_ptr[i];
+    if (len < 1 || len > N) atomicOr(&s_err, kErrRowPtr);
   }
   __syncthreads();
+  if (s_err) {
+    if (tid == 0) { st->iters = 0; st->status = VFPI_ERR_INVALID_ARG; st->err = s_err; st->theta = 0; }
+    return;
+  }
+  // each node in at most one contact (Prop. 3): claim it, a second claim fails
+  for (int m = tid; m < n_c; m += kThreads) {
+    const int i = node_i[m], j = node_j ? node_j[m] : -1;
+    if (i < 0 || i >= N || j < -1 || j >= N) { atomicOr(&s_err, kErrIndex); continue; }
+    if (i == j || atomicCAS(&cslot[i], -1, m) != -1) { atomicOr(&s_err, kErrOverlap); continue; }
+    if (j >= 0 && atomicCAS(&cslot[j], -1, m) != -1) atomicOr(&s_err, kErrOverlap);
+  }
+  __syncthreads();
+  if (s_err) {
+    if (tid == 0) { st->iters = 0; st->status = VFPI_ERR_INVALID_ARG; st->err = s_err; st->theta = 0; }
+    return;
+  }
   // W (Sec. IV.C): row statistics in FP64, tied on contact nodes
   for (int i = tid; i < N; i += kThreads) {
     double d[3] = {0, 0, 0}, q2[3] = {0, 0, 0};
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
       const int c = col_idx[p];
-      if (c < 0 || c >= N) { atomicOr(&s_err, 1); continue; }
+      if (c < 0 || c >= N) { atomicOr(&s_err, kErrIndex); continue; }
       const float* m = vals + 9ll * p;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -136,7 +158,6 @@ k_solve_noalloc(int N, const int32_t* __restrict__ row_ptr, const int32_t* __res
   __syncthreads();
   for (int m = tid; m < n_c; m += kThreads) {
     const int i = node_i[m], j = node_j ? node_j[m] : -1;
-    if (i < 0 || i >= N || j < -1 || j >= N) continue;
     double num = sums[i].x, den = sums[i].y;
     if (j >= 0) { num += sums[j].x; den += sums[j].y; }
     const float wb = (float)(num / den);
@@ -268,6 +289,8 @@ extern "C" vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b,
   if (N < 1 || N > kMaxNodes)
     return fail(VFPI_ERR_INVALID_ARG, "n_nodes must be 1..VFPI_NOALLOC_MAX_NODES (4096)");
   if (n_c < 0 || n_c > N) return fail(VFPI_ERR_INVALID_ARG, "n_c must be 0..n_nodes");
+  if (A->nnzb < N || (int64_t)A->nnzb > (int64_t)N * N)
+    return fail(VFPI_ERR_INVALID_ARG, "nnzb must be n_nodes..n_nodes^2 (every row holds 1..n_nodes blocks)");
   if (l_max < 1) return fail(VFPI_ERR_INVALID_ARG, "l_max must be >= 1");
   if (residual_norm != VFPI_NORM_ABS && residual_norm != VFPI_NORM_RMS)
     return fail(VFPI_ERR_INVALID_ARG, "unknown residual_norm");
@@ -305,7 +328,7 @@ extern "C" vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b,
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const double nscale = residual_norm == VFPI_NORM_RMS ? 1.0 / std::sqrt(3.0 * N) : 1.0;
   k_solve_noalloc<<<1, kThreads, 0, s>>>(
-      N, A->row_ptr, A->col_idx, static_cast<const float*>(A->vals), b, n_c,
+      N, A->nnzb, A->row_ptr, A->col_idx, static_cast<const float*>(A->vals), b, n_c,
       n_c ? Jc->node_i : nullptr, n_c ? Jc->node_j : nullptr,
       n_c ? static_cast<const float*>(Jc->R) : nullptr, n_c ? static_cast<const float*>(Jc->mu) : nullptr,
       n_c ? static_cast<const float*>(Jc->phi) : nullptr, theta_th, l_max, nscale, v_in, v_out,
@@ -323,7 +346,12 @@ extern "C" vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b,
   }
   if (iters_out) *iters_out = h.iters;
   if (theta_out) *theta_out = h.theta;
-  if (h.status == VFPI_ERR_INVALID_ARG) return fail(VFPI_ERR_INVALID_ARG, "a node or column index is out of range");
+  if (h.status == VFPI_ERR_INVALID_ARG) {
+    if (h.err & kErrRowPtr)
+      return fail(VFPI_ERR_INVALID_ARG, "row_ptr must run from 0 to nnzb with 1..n_nodes blocks per row");
+    if (h.err & kErrIndex) return fail(VFPI_ERR_INVALID_ARG, "a node or column index is out of range");
+    return fail(VFPI_ERR_CONTACT_OVERLAP, "a node is in two contacts (or a D-contact joins a node to itself)");
+  }
   if (h.status == VFPI_ERR_NONFINITE) return fail(VFPI_ERR_NONFINITE, "non-finite residual");
   return static_cast<vfpi_status>(h.status);
 }
