@@ -43,7 +43,7 @@ ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under
 # ncu DRAM traffic (read + write bytes per sweep) of the single-scene solve
 # kernel, keyed by (hash of the CUDA sources it was captured from, kernel
 # variant), each captured at the variant's default CTA count; stale entries
-# read as null (profiles/k_solve_grid_terrain_lattice_128x128x32.md)
+# read as null (the grid kernel's ncu summary gives the captures)
 NCU_TRAFFIC = {("30b2c5814acd1015", 0): 554449911, ("30b2c5814acd1015", 7): 553640967}
 
 
@@ -242,20 +242,38 @@ def batched_bench(args, torch, dev, stream, rank):
         s.get_velocity(out=v)
 
     n_dof = 3 * nq
+    nc_q = np.bincount(np.searchsorted(sc.scene_ptr, sc.node_i, side="right") - 1, minlength=S)
+    bytes_scene = np.array([
+        algorithmic_bytes_per_sweep(type("Q", (), dict(n_nodes=int(n), n=3 * int(n), nnzb=int(bq), n_c=int(c)))())
+        for n, bq, c in zip(nq, np.diff(sc.row_ptr[sc.scene_ptr]), nc_q)])
+    launch_log = []
 
-    def timed_steps():
+    def log_launch(kind):
+        # the solve launches in program order, each with its own algorithmic
+        # byte count (per-scene sweeps x per-scene bytes), so that a profiler
+        # capture of launch k can be set against its count
+        it, _, _ = s.status()
+        launch_log.append({"launch": len(launch_log), "kind": kind,
+                           "scene_sweeps": int(it.sum()),
+                           "alg_bytes": int((it * bytes_scene).sum())})
+
+    def timed_steps(log=False):
         # from the initial state: warm-up steps, one graph per env step, timed replays
         x.copy_(x0)
         v.copy_(T(sc.v0, np.float32))
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 env_step()
+                if log:
+                    log_launch("warm-up")
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
                 env_step()
             for _ in range(2):
                 g.replay()
+                if log:
+                    log_launch("replay before timing")
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             dof_iters, kms, its = 0, [], []
@@ -270,19 +288,17 @@ def batched_bench(args, torch, dev, stream, rank):
                 its.append(it.copy())
                 dof_iters += int((n_dof * it).sum())
                 kms.append(s.last_kernel_ms())
+                if log and len(launch_log) < args.warmup + 5:
+                    log_launch("timed")
         return t_total, np.array(its), dof_iters, kms
 
-    t_total, its, dof_iters, kms = timed_steps()
+    t_total, its, dof_iters, kms = timed_steps(log=True)
     # the same env steps with Chebyshev acceleration (Alg. 3) of the solves:
     # the same stop test, reached in fewer sweeps
     s.set_chebyshev(*BATCH_CHEBYSHEV)
     t_cheb, its_cheb, _, _ = timed_steps()
     s.set_chebyshev(0)
     env_sps = S * args.batch_steps / t_total
-    nc_q = np.bincount(np.searchsorted(sc.scene_ptr, sc.node_i, side="right") - 1, minlength=S)
-    bytes_scene = np.array([
-        algorithmic_bytes_per_sweep(type("Q", (), dict(n_nodes=int(n), n=3 * int(n), nnzb=int(bq), n_c=int(c)))())
-        for n, bq, c in zip(nq, np.diff(sc.row_ptr[sc.scene_ptr]), nc_q)])
     alg = float((its * bytes_scene[None, :]).sum(axis=1).mean())
     k_avg = float(np.mean(kms)) / 1e3
     # plain per-scene solves (one context per scene) on a sample, same tolerance
@@ -304,7 +320,8 @@ def batched_bench(args, torch, dev, stream, rank):
             per_ms.append(s1.last_kernel_ms())
     per_scene_total = float(np.mean(per_ms)) / 1e3 * S
     first_batch = kms[0] / 1e3
-    threads = s.layout()["threads"]
+    lay_b = s.layout()
+    threads = lay_b["threads"]
     var = int(tuned.get("kernel_variant", 0))
     kname = (f"k_solve_cluster<float,{threads}> (launch shape {var})" if var >= 16
              else f"k_solve_scenes<float,{threads}>")
@@ -317,6 +334,9 @@ def batched_bench(args, torch, dev, stream, rank):
         "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
                          "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0]},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
+        "layout": {"blocks": int(sc.nnzb), "stored_slots": int(lay_b["slots"]),
+                   "padding": lay_b["slots"] / sc.nnzb - 1.0},
+        "launch_log": launch_log,
         "with_chebyshev": {"l_s_u": list(BATCH_CHEBYSHEV),
                            "env_steps_per_s": S * args.batch_steps / t_cheb,
                            "ms_per_env_step": 1e3 * t_cheb / args.batch_steps,

@@ -595,37 +595,66 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   } else {
     c->h_scene_ptr[1] = N;
   }
-  // internal numbering: every scene padded to a multiple of 32 rows
-  c->h_node_map.resize(N);
-  c->h_node_scene.resize(N);
-  c->h_scene_slice.assign(c->n_scenes + 1, 0);
-  int64_t base = 0;
-  for (int q = 0; q < c->n_scenes; ++q) {
-    c->h_scene_slice[q] = (int32_t)(base / 32);
-    for (int i = c->h_scene_ptr[q]; i < c->h_scene_ptr[q + 1]; ++i) {
-      c->h_node_map[i] = (int32_t)(base + (i - c->h_scene_ptr[q]));
-      c->h_node_scene[i] = q;
-    }
-    base += (int64_t)round_up(c->h_scene_ptr[q + 1] - c->h_scene_ptr[q], 32);
-  }
-  if (base > INT32_MAX) { c->err = "too many padded rows"; return fail(VFPI_ERR_INVALID_ARG); }
-  c->n_pad = (int)base;
-  c->n_slices = c->n_pad / 32;
-  c->h_scene_slice[c->n_scenes] = c->n_slices;
-
-  // row pointers on the host: check and derive the slice lengths
+  // row pointers on the host: check them; every row's block count decides the
+  // internal numbering and the slice lengths
   std::vector<int32_t> row_ptr(N + 1);
   CREATE_CUDA(to_host(row_ptr.data(), A->row_ptr, 4 * ((size_t)N + 1), c->stream));
   if (row_ptr[0] != 0 || row_ptr[N] != A->nnzb) {
     c->err = "row_ptr must start at 0 and end at nnzb";
     return fail(VFPI_ERR_INVALID_ARG);
   }
-  c->h_slice_len.assign(c->n_slices, 0);
   for (int i = 0; i < N; ++i) {
     const int len = row_ptr[i + 1] - row_ptr[i];
     if (len < 1 || len > N) { c->err = "row_ptr: every row needs 1..n_nodes blocks"; return fail(VFPI_ERR_INVALID_ARG); }
+  }
+  auto row_len = [&](int i) { return row_ptr[i + 1] - row_ptr[i]; };
+
+  // internal numbering: every scene padded to a multiple of 32 rows.  A slice
+  // (32 rows) is padded to its longest row; within a scene whose rows differ
+  // in length (the boundary rows of a small lattice), ordering the rows by
+  // block count, longest first and otherwise in the given order, gives
+  // slices of similar rows.  That order is taken where it stores more than
+  // 2 % fewer slots than the given one -- a choice made from the scene's own
+  // rows, so a scene gets the same layout alone or in a batch.  The row
+  // arithmetic is the same in either order.
+  c->h_node_map.resize(N);
+  c->h_node_scene.resize(N);
+  c->h_scene_slice.assign(c->n_scenes + 1, 0);
+  int64_t base = 0;
+  std::vector<int32_t> rows_q;
+  auto padded_slots = [&](const std::vector<int32_t>& rows) {
+    int64_t slots = 0;
+    for (size_t k = 0; k < rows.size(); k += 32) {
+      int32_t m = 0;
+      for (size_t t = k; t < std::min(rows.size(), k + 32); ++t) m = std::max(m, row_len(rows[t]));
+      slots += 32 * (int64_t)m;
+    }
+    return slots;
+  };
+  for (int q = 0; q < c->n_scenes; ++q) {
+    const int s0 = c->h_scene_ptr[q], s1 = c->h_scene_ptr[q + 1];
+    c->h_scene_slice[q] = (int32_t)(base / 32);
+    rows_q.resize(s1 - s0);
+    std::iota(rows_q.begin(), rows_q.end(), s0);
+    const int64_t given = padded_slots(rows_q);
+    std::stable_sort(rows_q.begin(), rows_q.end(), [&](int a, int b) { return row_len(a) > row_len(b); });
+    const int64_t sorted = padded_slots(rows_q);
+    const bool use_sorted = sorted * 50 < given * 49;
+    for (int k = 0; k < s1 - s0; ++k) {
+      const int i = use_sorted ? rows_q[k] : s0 + k;
+      c->h_node_map[i] = (int32_t)(base + k);
+      c->h_node_scene[i] = q;
+    }
+    base += (int64_t)round_up(s1 - s0, 32);
+  }
+  if (base > INT32_MAX) { c->err = "too many padded rows"; return fail(VFPI_ERR_INVALID_ARG); }
+  c->n_pad = (int)base;
+  c->n_slices = c->n_pad / 32;
+  c->h_scene_slice[c->n_scenes] = c->n_slices;
+  c->h_slice_len.assign(c->n_slices, 0);
+  for (int i = 0; i < N; ++i) {
     int32_t& sl = c->h_slice_len[c->h_node_map[i] / 32];
-    sl = std::max(sl, len);
+    sl = std::max(sl, row_len(i));
   }
   c->h_slice_off.assign(c->n_slices, 0);
   int64_t ent = 0;
