@@ -9,7 +9,9 @@ FP64.  ``value`` is DOF x sweeps / device time (DOF-iterations per second).
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
 (a bounded number of sweeps per step).  Under torchrun each rank runs an
-independent replica (a single scene does not shard without an exchange step).
+independent replica (``value``, weak scaling); the same scene is then also
+split into one z-slab per rank and solved with a halo exchange per sweep over
+NCCL (key ``sharded``, strong scaling).
 """
 from __future__ import annotations
 
@@ -349,6 +351,36 @@ def batched_bench(args, torch, dev, stream, rank):
     }
 
 
+def sharded_bench(args, torch, dist, dev, sc, dims, rank, ws):
+    """The single scene split into one z-slab per rank (a shard context per
+    rank with its halo), Alg. 1 with the halo rows exchanged and the FP64
+    residual summed over NCCL every sweep; whole-scene DOF-iterations per
+    second over the slowest rank's time."""
+    from paper_2201_09212_gb300 import shard
+    ranges = shard.partition(sc.row_ptr, ws, align=dims[0] * dims[1])
+    plan = shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, rank)
+    comm = shard.TorchComm(dist, dev)
+    v0 = torch.from_numpy(np.ascontiguousarray(sc.v0[3 * plan.n0:3 * plan.n1])).to(dev)
+    kw = dict(n_dof=sc.n, theta_th=THETA_TH, l_max=L_MAX, norm="rms", device=dev)
+    with shard.shard_solver(sc, plan) as eng:
+        for _ in range(args.warmup):
+            shard.solve(eng, plan, comm, v0, **kw)
+        iters = []
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.sharded_steps):
+            iters.append(shard.solve(eng, plan, comm, v0, **kw).iters)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    _, t, _ = aggregate(dist, dev, t, 0.0)
+    return {"workload": f"{WORKLOAD} in {ws} z-slabs", "ranges": ranges,
+            "halo_nodes": int(len(plan.halo)), "steps": args.sharded_steps,
+            "iters_per_step": float(np.mean(iters)), "ms_per_step": 1e3 * t / args.sharded_steps,
+            "dof_iters_per_s": sc.n * float(np.sum(iters)) / t, "scaling": "strong",
+            "note": "one launch and one host round trip per sweep (exchange, residual sum)"}
+
+
 def configs_bench(args, torch, dev, stream):
     """The other plain-V-FPI configurations, each solved from its initial
     state repeatedly (tuned launch shape; a 256 MB write between steps flushes
@@ -476,6 +508,8 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=64)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--sharded-steps", type=int, default=10)
+    ap.add_argument("--no-sharded", action="store_true")
     ap.add_argument("--grid-variant", type=int, default=None,
                     help="fix the single scene's launch shape instead of tuning it")
     args = ap.parse_args()
@@ -592,6 +626,10 @@ def main():
     h2d = 4 * (sc.n + sc.n_c + sc.n) + 8 * sc.n
     d2h = 4 * (sc.n + 3 * sc.n_c) + 8 * sc.n
 
+    sharded = None
+    if ws > 1 and not args.no_sharded:
+        sharded = sharded_bench(args, torch, dist, dev, sc, dims, rank, ws)
+
     batched = None
     if not args.no_batched:
         batched = batched_bench(args, torch, dev, stream, rank)
@@ -653,6 +691,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
+        "sharded": sharded,
         "batched": batched,
         "adjoint": adjoint,
         "configs": configs,

@@ -129,7 +129,11 @@ typedef struct {
                               iteration of Alg. 1                                 */
   double chebyshev_u;      /* Alg. 3 under-relaxation u in (0, 1] (1 = the printed
                               update of eq. chebyup)                               */
-  int32_t reserved[2];
+  int32_t n_halo;          /* 0, or: this context is one shard of a scene split by
+                              rows across processes/GPUs (see "Sharded scene"
+                              below); A's columns then index its n_nodes own
+                              nodes and n_halo halo nodes owned by other shards  */
+  int32_t reserved;
 } vfpi_opts;
 
 /* Grid-path kernel variants (threads per CTA / minimum CTAs per SM the register
@@ -382,6 +386,44 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
                                double theta_th, int32_t l_max, int32_t residual_norm,
                                const float* v_in, float* v_out, float* lambda_out,
                                int32_t* iters_out, double* theta_out, void* cuda_stream);
+/* ------------------------------------------------------------------------
+ * Sharded scene.  Only the product A v couples nodes (Sec. III.F); the
+ * contact step of Alg. 2 is local to a contact's node(s).  So one scene can be
+ * split by rows: each shard owns a contiguous range of nodes (on the lattices
+ * here, a slab of z-layers), keeps their rows of A, b, W and their contacts,
+ * and per sweep needs the latest v of its halo -- the other shards' nodes that
+ * its rows reference -- plus the sum of every shard's ||dv||^2 for theta.
+ *
+ * vfpi_create with opts.n_halo > 0 makes such a shard: A has n_nodes rows (its
+ * own nodes); a column index c < n_nodes is own node c, c >= n_nodes is halo
+ * node c - n_nodes.  A row's columns need not increase (keep the unsplit
+ * scene's order and the row sums are bit for bit those of the unsplit scene)
+ * but each appears once, the diagonal block included.  Contacts join own nodes
+ * only (a contact across shards gives VFPI_ERR_INVALID_ARG).  A shard runs on
+ * the grid path (full storage), without Chebyshev, Barzilai-Borwein steps,
+ * the adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).
+ *
+ * A sweep of the whole scene is then: every shard calls vfpi_shard_sweep; the
+ * callers sum the shards' sumsq (theta^2 of Alg. 1 = the sum; rms: / n of the
+ * whole scene) and take the stop test; each shard reads the rows its
+ * neighbours need with vfpi_get_nodes and sets the rows it receives with
+ * vfpi_set_halo.  The package's shard module drives this over
+ * torch.distributed (NCCL between GPUs); nothing here communicates.
+ * ---------------------------------------------------------------------- */
+
+/* One sweep (eq. pgd1, Alg. 2, eq. vup) of this shard's rows from its current
+ * iterate and the halo values last set; the iterate advances.  sumsq_out
+ * (host double, nullable): this shard's FP64 sum of ||v^{l+1} - v^l||^2 over
+ * its rows, in a fixed order.  Synchronises the stream when sumsq_out is set. */
+vfpi_status vfpi_shard_sweep(vfpi_t ctx, double* sumsq_out);
+/* Copy the current v of own nodes nodes[0..n) (indices < n_nodes, host or
+ * device array) into out [3n] (host or device).  An index out of range gives
+ * VFPI_ERR_INVALID_ARG (checked on the device; out is then not written). */
+vfpi_status vfpi_get_nodes(vfpi_t ctx, const int32_t* nodes, int32_t n, void* out);
+/* Set the v of halo nodes [first, first + n) from vals [3n] (host or device);
+ * 0 <= first, first + n <= n_halo. */
+vfpi_status vfpi_set_halo(vfpi_t ctx, int32_t first, int32_t n, const void* vals);
+
 /* Message for the last failing vfpi_solve_noalloc call of this host thread. */
 const char* vfpi_noalloc_last_error(void);
 

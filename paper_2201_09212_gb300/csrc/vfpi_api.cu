@@ -127,7 +127,7 @@ void free_all(vfpi_ctx* c) {
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
                   c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
                   c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos,
-                  c->d_thscene, c->d_slicesq};
+                  c->d_thscene, c->d_slicesq, c->d_sumsq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -462,7 +462,8 @@ vfpi_status set_values(vfpi_ctx* c, const int32_t* drow, const int32_t* dcol, co
   if (st != VFPI_OK) return st;
   if (flags) return arg_fail(c, VFPI_ERR_NONFINITE, "A has non-finite values");
   VFPI_TRY_CUDA(DISPATCH(c, build_layout(c, drow, dcol, dv, store_cols)));
-  if (c->path == 1) return set_sym(c, dcol, dv, store_cols);
+  // (a shard keeps the full storage: its rows see halo columns outside A's square)
+  if (c->path == 1 && c->n_halo == 0) return set_sym(c, dcol, dv, store_cols);
   return VFPI_OK;
 }
 
@@ -547,6 +548,16 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "block_threads must be 0, 64, 128, 256 or 512");
   if (o->chebyshev_ls != 0 && (o->chebyshev_ls < 4 || !(o->chebyshev_u > 0 && o->chebyshev_u <= 1)))
     return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
+  if (o->n_halo < 0 || (int64_t)A->n_nodes + o->n_halo > INT32_MAX / 32)
+    return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "n_halo must be >= 0 (and the halo not too large)");
+  if (o->n_halo > 0) {
+    if (o->n_scenes > 1)
+      return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "a shard (n_halo > 0) is one scene");
+    if (o->force_path == 2)
+      return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "a shard runs on the grid path");
+    if (o->chebyshev_ls != 0)
+      return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "a shard runs plain sweeps (no Chebyshev)");
+  }
 
   vfpi_ctx* c = new (std::nothrow) vfpi_ctx;
   if (!c) return arg_fail(nullptr, VFPI_ERR_OOM, "host allocation failed");
@@ -558,6 +569,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   c->N = A->n_nodes;
   c->nnzb = A->nnzb;
   c->n_scenes = o->n_scenes > 1 ? o->n_scenes : 1;
+  c->n_halo = o->n_halo;
 
   auto fail = [&](vfpi_status st) {
     g_create_error = c->err;
@@ -647,10 +659,14 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
     }
     base += (int64_t)round_up(s1 - s0, 32);
   }
-  if (base > INT32_MAX) { c->err = "too many padded rows"; return fail(VFPI_ERR_INVALID_ARG); }
+  if (base + c->n_halo > INT32_MAX) { c->err = "too many padded rows"; return fail(VFPI_ERR_INVALID_ARG); }
   c->n_pad = (int)base;
   c->n_slices = c->n_pad / 32;
   c->h_scene_slice[c->n_scenes] = c->n_slices;
+  // a shard's halo nodes: read by the row products, stored after the padded
+  // rows (no slice covers them, so no sweep writes them)
+  c->h_node_map.resize((size_t)N + c->n_halo);
+  for (int k = 0; k < c->n_halo; ++k) c->h_node_map[(size_t)N + k] = c->n_pad + k;
   c->h_slice_len.assign(c->n_slices, 0);
   for (int i = 0; i < N; ++i) {
     int32_t& sl = c->h_slice_len[c->h_node_map[i] / 32];
@@ -664,8 +680,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   }
   c->n_entries = ent;
 
-  // device allocations
-  const size_t vec = c->esz * 4 * (size_t)c->n_pad;
+  // device allocations (the iterates hold a shard's halo after its rows)
+  const size_t vec = c->esz * 4 * ((size_t)c->n_pad + c->n_halo);
   CREATE_CUDA(dalloc(&c->d_slice_len, 4 * (size_t)c->n_slices));
   CREATE_CUDA(dalloc(&c->d_slice_off, 8 * (size_t)c->n_slices));
   CREATE_CUDA(dalloc(&c->d_slice_cmin, 4 * (size_t)std::max(c->n_slices, 1)));
@@ -679,7 +695,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_CUDA(dalloc(&c->d_t0, vec));
   CREATE_CUDA(dalloc(&c->d_t1, vec));
   CREATE_CUDA(dalloc(&c->d_cslot, 4 * (size_t)c->n_pad));
-  CREATE_CUDA(dalloc(&c->d_node_map, 4 * (size_t)N));
+  CREATE_CUDA(dalloc(&c->d_node_map, 4 * ((size_t)N + c->n_halo)));
+  CREATE_CUDA(dalloc(&c->d_sumsq, 8));
   CREATE_CUDA(dalloc(&c->d_row_ptr, 4 * ((size_t)N + 1)));
   CREATE_CUDA(cudaMemcpyAsync(c->d_row_ptr, row_ptr.data(), 4 * ((size_t)N + 1), cudaMemcpyHostToDevice, c->stream));
   CREATE_CUDA(dalloc(&c->d_ds, 8 * 6 * (size_t)c->n_pad));
@@ -700,7 +717,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   cudaStream_t st = c->stream;
   CREATE_CUDA(cudaMemcpyAsync(c->d_slice_len, c->h_slice_len.data(), 4 * (size_t)c->n_slices, cudaMemcpyHostToDevice, st));
   CREATE_CUDA(cudaMemcpyAsync(c->d_slice_off, c->h_slice_off.data(), 8 * (size_t)c->n_slices, cudaMemcpyHostToDevice, st));
-  CREATE_CUDA(cudaMemcpyAsync(c->d_node_map, c->h_node_map.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, st));
+  CREATE_CUDA(cudaMemcpyAsync(c->d_node_map, c->h_node_map.data(), 4 * ((size_t)N + c->n_halo),
+                              cudaMemcpyHostToDevice, st));
   CREATE_CUDA(cudaMemcpyAsync(c->d_scene_slice, c->h_scene_slice.data(), 4 * ((size_t)c->n_scenes + 1), cudaMemcpyHostToDevice, st));
   // largest scene first; per-scene norm scale
   std::vector<int32_t> order(c->n_scenes);
@@ -740,19 +758,22 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_CUDA(device_view(c, c->h_node_scene.data(), 4 * (size_t)N, off_scene,
                           reinterpret_cast<const void**>(&dscene)));
   CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-  CREATE_CUDA(DISPATCH(c, validate_pattern(N, drow, dcol, dscene, c->d_err, st)));
+  CREATE_CUDA(DISPATCH(c, validate_pattern(N, N + c->n_halo, c->n_halo == 0 ? 1 : 0, drow, dcol,
+                                           dscene, c->d_err, st)));
   {
     int flags = 0;
     CREATE_ST(read_err(c, &flags));
     if (flags) {
       c->err = std::string("A: invalid block pattern (") + ((flags & 1) ? "column out of range " : "") +
-               ((flags & 2) ? "columns not strictly increasing " : "") +
+               ((flags & 2) ? (c->n_halo ? "column repeated in a row " : "columns not strictly increasing ")
+                            : "") +
                ((flags & 4) ? "block couples two scenes " : "") + ((flags & 16) ? "missing diagonal block" : "") + ")";
       return fail(VFPI_ERR_INVALID_ARG);
     }
   }
   // kernel path (the grid path keeps A in symmetric storage as well, built by set_values)
   c->path = o->force_path ? o->force_path : (c->n_scenes > 1 || c->n_slices <= 64 ? 2 : 1);
+  if (c->n_halo > 0) c->path = 1;
   if (c->path != 1 && c->path != 2) { c->err = "force_path must be 0, 1 or 2"; return fail(VFPI_ERR_INVALID_ARG); }
   if (c->path == 1 && c->n_scenes > 1) { c->err = "the grid-wide path solves one scene"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_ST(set_values(c, drow, dcol, A->vals, true, off_vals));
@@ -797,6 +818,12 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
 #define CTX_CHECK(c)                                                            \
   do {                                                                          \
     if (!(c)) return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "context is NULL"); \
+  } while (0)
+// calls that need the whole scene (or the sweeps of one launch to meet no
+// halo) are not available on a shard
+#define NOT_ON_SHARD(c, what)                                                              \
+  do {                                                                                     \
+    if ((c)->n_halo > 0) return arg_fail(c, VFPI_ERR_UNSUPPORTED, what " is not available on a shard"); \
   } while (0)
 
 vfpi_status vfpi_update(vfpi_t c, const void* A_vals, const void* b, const vfpi_contacts* Jc) {
@@ -904,6 +931,7 @@ vfpi_status vfpi_set_friction(vfpi_t c, const void* mu) {
 vfpi_status vfpi_adjoint(vfpi_t c, const void* lambda_star, const void* g_v, void* g_b,
                          void* g_phi, void* g_mu, int32_t* iters_out, double* theta_out) {
   CTX_CHECK(c);
+  NOT_ON_SHARD(c, "vfpi_adjoint");
   if (!g_v) return arg_fail(c, VFPI_ERR_INVALID_ARG, "g_v is NULL");
   if (c->aniso)
     return arg_fail(c, VFPI_ERR_UNSUPPORTED, "the adjoint of elliptic friction cones is not built");
@@ -1001,6 +1029,7 @@ vfpi_status vfpi_get_scene_status(vfpi_t c, int32_t* status_out) {
 
 vfpi_status vfpi_solve_async(vfpi_t c) {
   CTX_CHECK(c);
+  NOT_ON_SHARD(c, "a multi-sweep solve (use vfpi_shard_sweep)");
   VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, false)));
   return VFPI_OK;
 }
@@ -1018,8 +1047,56 @@ vfpi_status vfpi_step(vfpi_t c, double* theta_out) {
   return st == VFPI_NOT_CONVERGED ? VFPI_OK : st;
 }
 
+vfpi_status vfpi_shard_sweep(vfpi_t c, double* sumsq_out) {
+  CTX_CHECK(c);
+  if (c->path != 1) return arg_fail(c, VFPI_ERR_UNSUPPORTED, "shard sweeps run on the grid path");
+  // one sweep: l_max = 1, never "converged" early; the kernel leaves the
+  // sweep's FP64 sum of squares in d_sumsq
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, 1, -1.0, false)));
+  if (!sumsq_out) return VFPI_OK;
+  double s2 = 0.0;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(&s2, c->d_sumsq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const vfpi_status st = vfpi_get_status(c, nullptr, nullptr);   // synchronises
+  *sumsq_out = s2;
+  return st == VFPI_NOT_CONVERGED ? VFPI_OK : st;
+}
+
+vfpi_status vfpi_get_nodes(vfpi_t c, const int32_t* nodes, int32_t n, void* out) {
+  CTX_CHECK(c);
+  if (n < 0 || (n > 0 && (!nodes || !out)))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "nodes and out are required (n >= 0)");
+  if (n == 0) return VFPI_OK;
+  const size_t bytes = c->esz * 3 * (size_t)n;
+  const size_t slot = round_up(4 * (size_t)n, 256);
+  VFPI_TRY_CUDA(ensure_stage(c, slot + bytes));
+  const void* dn;
+  void* dst;
+  VFPI_TRY_CUDA(device_view(c, nodes, 4 * (size_t)n, 0, &dn));
+  VFPI_TRY_CUDA(out_view(c, out, bytes, slot, &dst));
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  VFPI_TRY_CUDA(DISPATCH(c, gather_nodes(c, static_cast<const int32_t*>(dn), n, dst)));
+  int flags = 0;
+  vfpi_status st = read_err(c, &flags);
+  if (st != VFPI_OK) return st;
+  if (flags) return arg_fail(c, VFPI_ERR_INVALID_ARG, "vfpi_get_nodes: node index out of range");
+  if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_halo(vfpi_t c, int32_t first, int32_t n, const void* vals) {
+  CTX_CHECK(c);
+  if (first < 0 || n < 0 || (int64_t)first + n > c->n_halo || (n > 0 && !vals))
+    return arg_fail(c, VFPI_ERR_INVALID_ARG, "halo range must lie in [0, n_halo)");
+  if (n == 0) return VFPI_OK;
+  const void* dv;
+  VFPI_TRY_CUDA(device_view(c, vals, c->esz * 3 * (size_t)n, 0, &dv));
+  VFPI_TRY_CUDA(DISPATCH(c, set_halo(c, first, n, dv)));
+  return VFPI_OK;
+}
+
 vfpi_status vfpi_solve(vfpi_t c, void* v_inout, void* lambda_out, int32_t* iters_out, double* theta_out) {
   CTX_CHECK(c);
+  NOT_ON_SHARD(c, "a multi-sweep solve (use vfpi_shard_sweep)");
   vfpi_status st;
   if (v_inout && (st = vfpi_set_velocity(c, v_inout)) != VFPI_OK) return st;
   if ((st = vfpi_solve_async(c)) != VFPI_OK) return st;
@@ -1047,6 +1124,7 @@ vfpi_status vfpi_integrate(vfpi_t c, double* x) {
 
 vfpi_status vfpi_matvec(vfpi_t c, const void* x, void* y) {
   CTX_CHECK(c);
+  NOT_ON_SHARD(c, "vfpi_matvec");
   if (!x || !y) return arg_fail(c, VFPI_ERR_INVALID_ARG, "x and y are required");
   const void* dx;
   VFPI_TRY_CUDA(device_view(c, x, c->esz * 3 * (size_t)c->N, 0, &dx));
@@ -1167,6 +1245,7 @@ vfpi_status vfpi_set_anisotropic_friction(vfpi_t c, const void* mu2) {
 
 vfpi_status vfpi_set_barzilai_borwein(vfpi_t c, int32_t rule, double alpha0) {
   CTX_CHECK(c);
+  if (rule) NOT_ON_SHARD(c, "Barzilai-Borwein");
   if (rule < 0 || rule > 3) return arg_fail(c, VFPI_ERR_INVALID_ARG, "rule must be 0..3");
   if (rule && !(alpha0 > 0 && std::isfinite(alpha0)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "alpha0 must be > 0");
@@ -1186,6 +1265,7 @@ vfpi_status vfpi_set_barzilai_borwein(vfpi_t c, int32_t rule, double alpha0) {
 
 vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
+  if (l_s) NOT_ON_SHARD(c, "Chebyshev acceleration");
   if (l_s != 0 && (l_s < 4 || !(u > 0 && u <= 1)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
   if (l_s && c->bb_rule)
@@ -1197,6 +1277,7 @@ vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
 
 vfpi_status vfpi_set_adjoint_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
+  if (l_s) NOT_ON_SHARD(c, "Chebyshev acceleration");
   if (l_s != 0 && (l_s < 4 || !(u > 0 && u <= 1)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
   c->adj_cheb_ls = l_s;

@@ -120,6 +120,7 @@ struct SolveCtl {
   int32_t smem_bytes;            // dynamic shared memory per CTA (cluster path)
   int32_t theta_rel;             // 1: the adjoint stops at theta < theta_th * ||b|| (same norm)
   const double* th_scene;        // grid path: [1] theta_th * ||b||, computed before the launch
+  double* sumsq;                 // grid path: [1] the last sweep's sum ||dv||^2 (before scaling)
 };
 
 
@@ -858,7 +859,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
+  double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -927,7 +928,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       if (threadIdx.x == 0) red[32] = s2w;
     }
     __syncthreads();
-    const double s2 = red[32];
+    s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
@@ -949,6 +950,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     ctl.iters[0] = l;
     ctl.theta[0] = theta;
     ctl.status[0] = st;
+    if (ctl.sumsq) ctl.sumsq[0] = s2;
   }
   if (st == ST_TIMEOUT && threadIdx.x == 0) atomicOr(ctl.err, 1);
 }
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   uint32_t phase = 0;  // bit q: parity of the next completion of stage q
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
-  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -1183,7 +1185,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
       if (threadIdx.x == 0) red[32] = s2w;
     }
     __syncthreads();
-    const double s2 = red[32];
+    s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
@@ -1203,6 +1205,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     ctl.iters[0] = l;
     ctl.theta[0] = theta;
     ctl.status[0] = st;
+    if (ctl.sumsq) ctl.sumsq[0] = s2;
   }
   if (st == ST_TIMEOUT && threadIdx.x == 0) atomicOr(ctl.err, 1);
 }
@@ -1862,7 +1865,12 @@ __global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl 
 
 // Validate the caller's BSR pattern: columns in range, strictly increasing,
 // diagonal present, no block across two scenes.  Error bits go to *err.
-static __global__ void k_validate_pattern(int N, const int32_t* __restrict__ row_ptr,
+// Columns in [0, n_cols) (n_cols = N, or N + the halo of a shard); increasing
+// (err 2) when `sorted`, else each once per row (a shard keeps the unsplit
+// scene's order, whose halo columns may sort below its own); the diagonal
+// present; no block coupling two scenes.
+static __global__ void k_validate_pattern(int N, int n_cols, int sorted,
+                                          const int32_t* __restrict__ row_ptr,
                                           const int32_t* __restrict__ col_idx,
                                           const int32_t* __restrict__ node_scene, int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1873,13 +1881,42 @@ static __global__ void k_validate_pattern(int N, const int32_t* __restrict__ row
   int prev = -1;
   for (int p = r0; p < r1; ++p) {
     const int c = col_idx[p];
-    if (c < 0 || c >= N) { atomicOr(err, 1); return; }
-    if (c <= prev) atomicOr(err, 2);
+    if (c < 0 || c >= n_cols) { atomicOr(err, 1); return; }
+    if (sorted) {
+      if (c <= prev) atomicOr(err, 2);
+    } else {
+      for (int q = r0; q < p; ++q)
+        if (col_idx[q] == c) atomicOr(err, 2);
+    }
     if (c == i) diag = true;
-    if (node_scene[c] != node_scene[i]) atomicOr(err, 4);
+    if (c < N && node_scene[c] != node_scene[i]) atomicOr(err, 4);
     prev = c;
   }
   if (!diag) atomicOr(err, 16);
+}
+
+// v of own nodes nodes[0..n) (caller's numbering) -> out [3n]; an index out of
+// range sets err bit 1 and is skipped.
+template <typename T>
+__global__ void k_gather_nodes(int n, int N, const int32_t* __restrict__ nodes,
+                               const int32_t* __restrict__ node_map, const Vec4<T>* __restrict__ v,
+                               T* __restrict__ out, int* err) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = nodes[k];
+  if (i < 0 || i >= N) { atomicOr(err, 1); return; }
+  const Vec4<T> q = ldv(v + node_map[i]);
+  out[3 * (int64_t)k] = q.x;
+  out[3 * (int64_t)k + 1] = q.y;
+  out[3 * (int64_t)k + 2] = q.z;
+}
+
+// vals [3n] -> v of halo nodes [first, first + n), stored after the padded rows.
+template <typename T>
+__global__ void k_set_halo(int n, int64_t base, const T* __restrict__ vals, Vec4<T>* __restrict__ v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  stv(v + base + k, Vec4<T>{vals[3 * (int64_t)k], vals[3 * (int64_t)k + 1], vals[3 * (int64_t)k + 2], T(0)});
 }
 
 template <typename T>

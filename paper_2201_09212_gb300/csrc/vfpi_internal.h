@@ -16,8 +16,12 @@ struct DevState;  // device pointers, see vfpi_ctx
 // Launchers, instantiated for float and double in vfpi_f32.cu / vfpi_f64.cu.
 template <typename T>
 struct Launch {
-  static cudaError_t validate_pattern(int N, const int32_t* row_ptr, const int32_t* col_idx,
-                                      const int32_t* node_scene, int* err, cudaStream_t s);
+  static cudaError_t validate_pattern(int N, int n_cols, int sorted, const int32_t* row_ptr,
+                                      const int32_t* col_idx, const int32_t* node_scene, int* err,
+                                      cudaStream_t s);
+  // sharded scene: v of own nodes out, halo values in
+  static cudaError_t gather_nodes(vfpi_ctx* c, const int32_t* nodes, int n, void* out);
+  static cudaError_t set_halo(vfpi_ctx* c, int first, int n, const void* vals);
   static cudaError_t check_finite(const void* a, int64_t n, int* err, cudaStream_t s);
   static cudaError_t build_layout(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx,
                                   const void* vals, bool store_cols);
@@ -50,6 +54,7 @@ struct vfpi_ctx {
 
   // sizes
   int N = 0, nnzb = 0, n_scenes = 1, n_slices = 0, n_pad = 0, n_c = 0, n_d = 0;
+  int n_halo = 0;         // shard of a split scene: halo nodes, stored after the n_pad rows
   int64_t n_entries = 0;  // sum of slice lengths; stored block slots = 32 * n_entries
 
   // host copies of the layout and contact bookkeeping
@@ -87,6 +92,7 @@ struct vfpi_ctx {
   int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
   double* d_norm_scale = nullptr;
   double* d_partials = nullptr;
+  double* d_sumsq = nullptr;                // the grid kernels' last sum ||dv||^2
   double* d_bbpart = nullptr;               // BB dot-product partials [2][max_grid][3]
   void *d_r0 = nullptr, *d_r1 = nullptr;    // BB residual ping-pong (allocated on use)
   int adj_cheb_ls = 0;                      // Chebyshev acceleration of the adjoint solve

@@ -62,9 +62,29 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::validate_pattern(int N, const int32_t* row_ptr, const int32_t* col_idx,
-                                        const int32_t* node_scene, int* err, cudaStream_t s) {
-  if (N > 0) k_validate_pattern<<<blocks_for(N, 256), 256, 0, s>>>(N, row_ptr, col_idx, node_scene, err);
+cudaError_t Launch<T>::validate_pattern(int N, int n_cols, int sorted, const int32_t* row_ptr,
+                                        const int32_t* col_idx, const int32_t* node_scene, int* err,
+                                        cudaStream_t s) {
+  if (N > 0)
+    k_validate_pattern<<<blocks_for(N, 256), 256, 0, s>>>(N, n_cols, sorted, row_ptr, col_idx,
+                                                          node_scene, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::gather_nodes(vfpi_ctx* c, const int32_t* nodes, int n, void* out) {
+  if (n > 0)
+    k_gather_nodes<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+        n, c->N, nodes, c->d_node_map, static_cast<const Vec4<T>*>(c->d_v0), static_cast<T*>(out),
+        c->d_err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::set_halo(vfpi_ctx* c, int first, int n, const void* vals) {
+  if (n > 0)
+    k_set_halo<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(
+        n, (int64_t)c->n_pad + first, static_cast<const T*>(vals), static_cast<Vec4<T>*>(c->d_v0));
   return cudaGetLastError();
 }
 
@@ -410,6 +430,7 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.smem_bytes = (int32_t)c->dyn_smem;
   ctl.theta_rel = (adjoint && c->adj_tol_set && c->adj_rel) ? 1 : 0;
   ctl.th_scene = c->d_thscene;
+  ctl.sumsq = c->d_sumsq;
   if (ctl.theta_rel && c->path == 1 && c->n_slices > 0) {   // (the per-scene kernels compute theirs)
     k_slice_sumsq<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
         c->n_slices, static_cast<const Vec4<T>*>(c->d_adj_g), c->d_slicesq);

@@ -38,7 +38,7 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
             "vfpi_set_barzilai_borwein",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
-            "vfpi_noalloc_last_error")
+            "vfpi_noalloc_last_error", "vfpi_shard_sweep", "vfpi_get_nodes", "vfpi_set_halo")
 
 
 class VfpiError(RuntimeError):
@@ -64,7 +64,7 @@ class _Opts(C.Structure):
                 ("scene_ptr", C.c_void_p), ("block_threads", C.c_int32),
                 ("force_path", C.c_int32), ("kernel_variant", C.c_int32),
                 ("grid_ctas", C.c_int32), ("chebyshev_ls", C.c_int32),
-                ("chebyshev_u", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("chebyshev_u", C.c_double), ("n_halo", C.c_int32), ("reserved", C.c_int32)]
 
 
 _LIB = None
@@ -118,6 +118,9 @@ def lib():
         "vfpi_destroy": (None, [vp]),
         "vfpi_solve_noalloc": (st, [vp, vp, vp, C.c_double, i32, i32, vp, vp, vp, vp, vp, vp]),
         "vfpi_noalloc_last_error": (C.c_char_p, []),
+        "vfpi_shard_sweep": (st, [vp, vp]),
+        "vfpi_get_nodes": (st, [vp, vp, i32, vp]),
+        "vfpi_set_halo": (st, [vp, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -178,7 +181,7 @@ class Solver:
                  dtype="f32", w_mode="frobenius", alpha=0.0, w_user=None, theta_th=1e-5,
                  l_max=200, norm="abs", scene_ptr=None, block_threads=0, force_path=0,
                  kernel_variant=0, grid_ctas=0, chebyshev_ls=0, chebyshev_u=1.0,
-                 operator="strict", stream=None):
+                 operator="strict", n_halo=0, stream=None):
         self._L = lib()
         self.dtype_code, self.np_dtype = DTYPES[dtype]
         self.n_nodes = int(len(row_ptr) - 1)
@@ -210,6 +213,8 @@ class Solver:
         o.grid_ctas = int(grid_ctas)
         o.chebyshev_ls = int(chebyshev_ls)
         o.chebyshev_u = float(chebyshev_u)
+        o.n_halo = int(n_halo)
+        self.n_halo = int(n_halo)
         self.h = float(h)
         self._theta_th, self._l_max = float(theta_th), int(l_max)
         self.stream = stream
@@ -293,6 +298,28 @@ class Solver:
         st = self._check(self._L.vfpi_get_status(self._h, iters.ctypes.data, theta.ctypes.data),
                          allow_nc=True)
         return iters, theta, st
+
+    # ---------------------------------------------------------- sharded scene
+    def shard_sweep(self) -> float:
+        """One sweep of this shard's rows (halo values as last set); returns the
+        shard's FP64 sum of squares of the update over its rows."""
+        s2 = C.c_double()
+        self._check(self._L.vfpi_shard_sweep(self._h, C.byref(s2)))
+        return float(s2.value)
+
+    def get_nodes(self, nodes, out=None):
+        """v of own nodes ``nodes`` (indices < n_nodes), [3 * len(nodes)]."""
+        out = self._out(3 * len(nodes), out)
+        k = _Keep()
+        self._check(self._L.vfpi_get_nodes(self._h, k.ptr(nodes, np.int32), int(len(nodes)),
+                                           k.ptr(out, self.np_dtype)))
+        return out
+
+    def set_halo(self, first, vals):
+        """v of halo nodes [first, first + len(vals) / 3)."""
+        k = _Keep()
+        self._check(self._L.vfpi_set_halo(self._h, int(first), int(len(vals) // 3),
+                                          k.ptr(vals, self.np_dtype)))
 
     def scene_status(self):
         """Per-scene outcome of the last solve or adjoint solve (status codes)."""

@@ -48,9 +48,10 @@ def test_struct_layout_matches_header(tmp_path):
         #include "vfpi.h"
         int main(void) {
           printf("%zu %zu %zu\\n", sizeof(vfpi_bsr), sizeof(vfpi_contacts), sizeof(vfpi_opts));
-          printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(vfpi_opts, theta_th), offsetof(vfpi_opts, l_max),
+          printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(vfpi_opts, theta_th), offsetof(vfpi_opts, l_max),
                  offsetof(vfpi_opts, scene_ptr), offsetof(vfpi_opts, force_path),
-                 offsetof(vfpi_contacts, phi), offsetof(vfpi_opts, chebyshev_u));
+                 offsetof(vfpi_contacts, phi), offsetof(vfpi_opts, chebyshev_u),
+                 offsetof(vfpi_opts, n_halo));
           return 0;
         }"""))
     exe = tmp_path / "layout"
@@ -66,6 +67,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert sizes[6] == vfpi._Opts.force_path.offset
     assert sizes[7] == vfpi._Contacts.phi.offset
     assert sizes[8] == vfpi._Opts.chebyshev_u.offset
+    assert sizes[9] == vfpi._Opts.n_halo.offset
 
 
 def test_host_only_entry_points(L):
