@@ -98,7 +98,7 @@ struct SolveCtl {
   double theta_th;
   const double* norm_scale;      // [n_scenes] 1 or 1/sqrt(n_q)
   double* partials;              // [2][grid] FP64 block partials (grid path)
-  unsigned int* bar;             // [2] barrier count, generation (grid path)
+  unsigned int* bar;             // [1] barrier arrivals, zeroed per launch (grid path)
   int32_t n_scenes;
   const int32_t* order;          // [n_scenes] processing order (largest first)
   const int32_t* scene_slice;    // [n_scenes+1]
@@ -793,35 +793,75 @@ __device__ __forceinline__ double block_allreduce(double x, double* red) {
 // All CTAs arrive; returns false if the wait ran out (the caller then stops).
 // Co-residency of all CTAs is guaranteed by the cooperative launch; the spin
 // is bounded anyway so that a fault elsewhere can never hang the GPU.
-// Release/acquire at GPU scope: each CTA's arrival (acq_rel) publishes what
-// the CTA wrote before it; the last arrival resets the count and publishes a
-// new generation (release), which the others read with acquire loads, so they
-// see every CTA's writes without a full fence.
+// One counter that only grows within a launch (zeroed before it): barrier k
+// of the launch is passed once it reads k * gridDim.x.  Each CTA arrives with
+// a posted reduction (red.release: nothing to wait for, unlike an atomic that
+// returns a ticket) that publishes what the CTA wrote before it; the wait
+// reads the counter with acquire loads, so a CTA that sees every arrival sees
+// every CTA's writes.  `nb` is the CTA's count of barriers passed times
+// gridDim.x (the same in every CTA: all take the same barriers).
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int& nb, int* s_ok) {
   __syncthreads();
+  nb += gridDim.x;
   if (threadIdx.x == 0) {
-    const unsigned int gen = ld_acquire_gpu(bar + 1);
-    unsigned int ticket;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(bar) : "memory");
-    int ok = 1;
-    if (ticket == gridDim.x - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-    } else {
-      ok = 0;
-      for (long long it = 0; it < kBarrierPolls; ++it) {
-        if (ld_acquire_gpu(bar + 1) != gen) { ok = 1; break; }
-        if (it > 64) __nanosleep(32);
-      }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    int ok = 0;
+    for (long long it = 0; it < kBarrierPolls; ++it) {
+      if (ld_acquire_gpu(bar) >= nb) { ok = 1; break; }
+      if (it > 64) __nanosleep(32);
     }
     *s_ok = ok;
   }
   __syncthreads();
+  return *s_ok != 0;
+}
+
+// End of a grid-wide sweep: the CTA's FP64 sum of its warps' partials, the
+// grid barrier (as grid_barrier) and the fixed-order sum of every CTA's
+// partial -- computed alike by every CTA, so all take the same stop decision
+// -- with two block barriers instead of six: warp 0 sums the warps' partials,
+// lane 0 publishes the CTA's sum and arrives and waits, __syncwarp passes its
+// acquire on to the warp, which sums the CTAs' partials; the other warps wait
+// at the second block barrier.  `part` is this sweep's half of the partials
+// (the other half may still be read by a CTA that is one barrier behind).
+template <int NT>
+__device__ __forceinline__ bool sweep_sum_barrier(double acc, double* part, unsigned int* bar,
+                                                  unsigned int& nb, double* red, int* s_ok,
+                                                  double* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  acc = warp_sum(acc);
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();   // every row of this sweep written, every warp's partial in red
+  nb += gridDim.x;
+  if (wid == 0) {
+    double y = lane < NT / 32 ? red[lane] : 0.0;
+    y = warp_sum(y);
+    int ok = 0;
+    if (lane == 0) {
+      part[blockIdx.x] = y;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+      for (long long it = 0; it < kBarrierPolls; ++it) {
+        if (ld_acquire_gpu(bar) >= nb) { ok = 1; break; }
+        if (it > 64) __nanosleep(32);
+      }
+    }
+    __syncwarp();
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    double s2w = 0.0;
+    for (int q = lane; q < (int)gridDim.x; q += 32) s2w += part[q];
+    s2w = warp_sum(s2w);
+    if (lane == 0) {
+      red[32] = s2w;
+      *s_ok = ok;
+    }
+  }
+  __syncthreads();
+  *total = red[32];
   return *s_ok != 0;
 }
 
@@ -859,6 +899,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
+  unsigned int nbar = 0;   // barriers passed x gridDim.x
   double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
@@ -887,7 +928,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
           bp[3 * blockIdx.x + 2] = zz;
         }
       }
-      if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+      if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
       if (l > 1) {
         const double* bp = ctl.bb_part + (size_t)(l & 1) * 3 * gridDim.x;
         double q0 = 0.0, q1 = 0.0, q2 = 0.0;
@@ -904,31 +945,23 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       for (int s = gw; s < P.n_slices; s += nw)
         acc += bb_update_row(P, s, lane, vin, vout, rcur, (T)bb_alpha);
       if (ctl.n_d > 0) {
-        if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+        if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
           acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
       }
     } else {
       for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF, SYM>(P, s, lane, vin, vout, ch);
       if (ctl.n_d > 0) {
-        if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+        if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
           acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
       }
     }
-    acc = block_allreduce<NT>(acc, red);
-    double* part = ctl.partials + (l & 1) * gridDim.x;
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
-    if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
-    // one warp sums the CTA partials (fixed order) and broadcasts the total
-    if (threadIdx.x < 32) {
-      double s2w = 0.0;
-      for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s2w += part[q];
-      s2w = warp_sum(s2w);
-      if (threadIdx.x == 0) red[32] = s2w;
+    if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
+                               &s2)) {
+      st = ST_TIMEOUT;
+      break;
     }
-    __syncthreads();
-    s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
@@ -1078,6 +1111,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   uint32_t phase = 0;  // bit q: parity of the next completion of stage q
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
+  unsigned int nbar = 0;   // barriers passed x gridDim.x
   double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
@@ -1169,23 +1203,15 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     }
     if (__syncthreads_or(failed ? 1 : 0)) { st = ST_TIMEOUT; break; }
     if (ctl.n_d > 0) {
-      if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
+      if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
       for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
         acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
-    acc = block_allreduce<NT>(acc, red);
-    double* part = ctl.partials + (l & 1) * gridDim.x;
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
-    if (!grid_barrier(ctl.bar, &s_ok)) { st = ST_TIMEOUT; break; }
-    // one warp sums the CTA partials (fixed order) and broadcasts the total
-    if (threadIdx.x < 32) {
-      double s2w = 0.0;
-      for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) s2w += part[q];
-      s2w = warp_sum(s2w);
-      if (threadIdx.x == 0) red[32] = s2w;
+    if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
+                               &s2)) {
+      st = ST_TIMEOUT;
+      break;
     }
-    __syncthreads();
-    s2 = red[32];
     theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
