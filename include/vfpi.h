@@ -183,7 +183,13 @@ enum {
   VFPI_VARIANT_CL_256_4_2 = 22,
   VFPI_VARIANT_CL_256_8_2 = 23,
   VFPI_VARIANT_CL_512_8_1 = 24,
-  VFPI_VARIANT_CL_128_8_4 = 25
+  VFPI_VARIANT_CL_128_8_4 = 25,
+  /* Grid path again: the TMA ring with two stages per warp (threads per CTA /
+   * stages): half the shared memory per warp of VFPI_VARIANT_TMA_256_4, so
+   * twice the warps fit -- for mid-size scenes whose sweeps are bounded by
+   * each warp's chain of dependent loads rather than by bandwidth. */
+  VFPI_VARIANT_TMA_256_2 = 26,
+  VFPI_VARIANT_TMA_128_2 = 27
 };
 
 /* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,

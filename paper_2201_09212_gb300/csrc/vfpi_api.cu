@@ -151,8 +151,10 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
   static const int sym_table[4][2] = {{256, 2}, {256, 3}, {256, 4}, {512, 1}};
   const bool is_cl = v >= VFPI_VARIANT_CL_256_1_1 && v <= VFPI_VARIANT_CL_128_8_4;
   const bool is_sym = v >= VFPI_VARIANT_SYM_256_2 && v <= VFPI_VARIANT_SYM_512_1;
-  if (v < 0 || (v > VFPI_VARIANT_SYM_512_1 && !is_cl)) return false;
+  const bool is_tma2 = v == VFPI_VARIANT_TMA_256_2 || v == VFPI_VARIANT_TMA_128_2;
+  if (v < 0 || (v > VFPI_VARIANT_SYM_512_1 && !is_cl && !is_tma2)) return false;
   if (c->path == 1 && is_cl) return false;
+  if (c->path != 1 && is_tma2) return false;
   if (is_sym && (c->path != 1 || !c->sym_ok)) return false;
   c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
   c->minb = 1;
@@ -165,6 +167,9 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
     c->nt = sym_table[v - VFPI_VARIANT_SYM_256_2][0];
     c->minb = sym_table[v - VFPI_VARIANT_SYM_256_2][1];
     c->sym = 1;
+  } else if (is_tma2) {
+    c->nt = v == VFPI_VARIANT_TMA_256_2 ? 256 : 128;
+    c->tma_stages = 2;
   } else if (c->path == 1 && (v > 0 || !block_threads)) {
     c->nt = grid_table[v][0];
     c->minb = grid_table[v][1];

@@ -277,7 +277,7 @@ static void* tma_kernel(int nt, int nst, bool adj, size_t* smem) {
     return adj ? (void*)&k_solve_grid_tma<T, NT_, NS_, true>                            \
                : (void*)&k_solve_grid_tma<T, NT_, NS_, false>;                          \
   }
-  VFPI_TK(256, 4) VFPI_TK(128, 4) VFPI_TK(128, 6) VFPI_TK(64, 8)
+  VFPI_TK(256, 4) VFPI_TK(128, 4) VFPI_TK(128, 6) VFPI_TK(64, 8) VFPI_TK(256, 2) VFPI_TK(128, 2)
 #undef VFPI_TK
   return nullptr;
 }

@@ -202,8 +202,8 @@ k_solve_noalloc(int N, int nnzb, const int32_t* __restrict__ row_ptr, const int3
         lambda_out[3 * cs + 2] = lam.z;
       }
       vout[i] = vn;
-      const double dx = (double)vn.x - vo.x, dy = (double)vn.y - vo.y, dz = (double)vn.z - vo.z;
-      acc += dx * dx + dy * dy + dz * dz;
+      const float dx = vn.x - vo.x, dy = vn.y - vo.y, dz = vn.z - vo.z;   // as sqdiff
+      acc += (double)(dx * dx + dy * dy + dz * dz);
     }
     if (node_j) {
       __syncthreads();
@@ -226,9 +226,9 @@ k_solve_noalloc(int N, int nnzb, const int32_t* __restrict__ row_ptr, const int3
         lambda_out[3 * m + 1] = lam.y;
         lambda_out[3 * m + 2] = lam.z;
         const float4 oi = vin[i], oj = vin[j];
-        const double e0 = (double)ni.x - oi.x, e1 = (double)ni.y - oi.y, e2 = (double)ni.z - oi.z;
-        const double f0 = (double)nj.x - oj.x, f1 = (double)nj.y - oj.y, f2 = (double)nj.z - oj.z;
-        acc += e0 * e0 + e1 * e1 + e2 * e2 + f0 * f0 + f1 * f1 + f2 * f2;
+        const float e0 = ni.x - oi.x, e1 = ni.y - oi.y, e2 = ni.z - oi.z;
+        const float f0 = nj.x - oj.x, f1 = nj.y - oj.y, f2 = nj.z - oj.z;
+        acc += (double)(e0 * e0 + e1 * e1 + e2 * e2) + (double)(f0 * f0 + f1 * f1 + f2 * f2);
       }
     }
     theta = sqrt(block_allreduce(acc, red)) * nscale;

@@ -26,9 +26,9 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
-GRID_VARIANTS = tuple(range(16))      # 12..15 need an exactly symmetric A
+GRID_VARIANTS = tuple(range(16)) + (26, 27)   # 12..15 need an exactly symmetric A
 WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2,
-         12: 8, 13: 8, 14: 8, 15: 16}
+         12: 8, 13: 8, 14: 8, 15: 16, 26: 8, 27: 4}
 CLUSTER_VARIANTS = tuple(range(16, 26))
 SPECIAL_MARGIN = 0.02
 
@@ -49,11 +49,13 @@ def _grid_candidates(n_slices, warps, max_grid, sms):
     return sorted(g for g in out if g == 0 or g <= max_grid)
 
 
-def _time(solver, sweeps, reps, v_start=None):
+def _time(solver, sweeps, reps, v_start=None, before_rep=None):
     best = float("inf")
     for _ in range(reps):
         if v_start is not None:
             solver.set_velocity(v_start)
+        if before_rep is not None:
+            before_rep()
         solver.solve_async()
         solver.status()
         best = min(best, solver.last_kernel_ms())
@@ -61,11 +63,17 @@ def _time(solver, sweeps, reps, v_start=None):
 
 
 def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CACHE,
-         force: bool = False) -> dict:
-    """Pick and apply the fastest launch shape; returns it with its timings."""
+         force: bool = False, before_rep=None, condition: str = "") -> dict:
+    """Pick and apply the fastest launch shape; returns it with its timings.
+
+    ``before_rep`` (optional) runs before every timed launch -- e.g. a write
+    that evicts L2, when the solves it tunes for follow other work; the ranking
+    of shapes depends on it (a mid-size scene whose matrix stays in L2 between
+    solves prefers other shapes than one that starts each solve from HBM).
+    ``condition`` names that setting in the cache key."""
     import torch
     gpu = torch.cuda.get_device_name()
-    key = _signature(solver, gpu)
+    key = _signature(solver, gpu) + (f"|{condition}" if condition else "")
     table = {}
     if cache and os.path.exists(cache):
         try:
@@ -90,7 +98,7 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
             l2 = solver.layout()
             for g in _grid_candidates(l2["n_slices"], WARPS[var], l2["max_grid"], l2["sms"]):
                 solver.configure_launch(var, 0, g)
-                ms = _time(solver, sweeps, reps)
+                ms = _time(solver, sweeps, reps, before_rep=before_rep)
                 trials.append(dict(kernel_variant=var, block_threads=0, grid_ctas=g,
                                    ms_per_sweep=ms / sweeps, grid=solver.layout()["grid"]))
     else:
@@ -105,7 +113,7 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
                 solver.configure_launch(var, bt, 0)
             except RuntimeError:    # shape not available on this GPU
                 continue
-            ms = _time(solver, sweeps, reps, v_start)
+            ms = _time(solver, sweeps, reps, v_start, before_rep)
             iters, _, _ = solver.status()
             trials.append(dict(kernel_variant=var, block_threads=bt, grid_ctas=0,
                                ms_per_sweep=ms / max(1.0, float(iters.max())), ms_per_solve=ms,

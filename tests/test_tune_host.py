@@ -104,7 +104,7 @@ def test_refused_shapes_are_skipped_and_tolerance_restored():
     s = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16))
     r = tune.tune(s, sweeps=10, reps=2, cache=None)
     tried = {t["kernel_variant"] for t in r["trials"]}
-    assert tried == set(range(12)) and s.tol == (1e-6, 200)
+    assert tried == set(range(12)) | {26, 27} and s.tol == (1e-6, 200)
     assert set(s.tol_at_launch) == {(-1.0, 10)}          # fixed sweep count, no stop test
     assert all(t["ms_per_sweep"] == pytest.approx(grid_cost(1.0)(t["kernel_variant"], 0,
                                                                    t["grid_ctas"]) / 10)
