@@ -46,7 +46,11 @@ ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under
 # kernel, keyed by (hash of the CUDA sources it was captured from, kernel
 # variant), each captured at the variant's default CTA count; stale entries
 # read as null (the grid kernel's ncu summary gives the captures)
-NCU_TRAFFIC = {("30b2c5814acd1015", 0): 554449911, ("30b2c5814acd1015", 7): 553640967}
+NCU_TRAFFIC = {("6860f7075873d4c3", 0): 554189273, ("6860f7075873d4c3", 7): 553468177}
+# the same for the batched kernel: (DRAM read + write bytes, algorithmic bytes)
+# of one captured env-step solve launch (the bench's launch log gives the
+# captured launch's own count), keyed by source hash
+NCU_BATCH_TRAFFIC = {"6860f7075873d4c3": (164302877184, 172972435132)}
 
 
 def source_hash() -> str:
@@ -158,6 +162,80 @@ def cpu_oracle_rate(sc, sweeps: int):
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     return sc.n * sweeps / dt, max(1, round(cpu / dt)), dt
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_block_worker(job, start, results):
+    """One core's share of the all-core CPU baseline: the unmodified FP64
+    oracle sweep (Alg. 1 + Alg. 2) on one z-slab of the scene -- its rows, and
+    its halo as identity rows with b = 0 so that the block is a square problem
+    -- timed over the same number of sweeps as the other workers, which start
+    together."""
+    from oracle import vfpi as ov
+    P = ov.make_problem(*job["problem"])
+    w = ov.frobenius_w(P)
+    v = np.asarray(job["v0"], dtype=np.float64)
+    ov.sweep(P, w, v)
+    start.wait()
+    t0 = time.perf_counter()
+    for _ in range(job["sweeps"]):
+        v = ov.sweep(P, w, v).v_next
+    results.put(time.perf_counter() - t0)
+
+
+def cpu_oracle_rate_all_cores(sc, dims, sweeps: int):
+    """The FP64 oracle's sweep over all host cores: the scene split into one
+    z-slab per core (the split of the multi-GPU path), every slab swept by the
+    oracle in its own process, all at once; DOF-iterations per second over the
+    slowest slab.  The halo exchange between sweeps is left out (the slabs'
+    sweeps are timed back to back), so this bounds an all-core oracle from
+    above.  Returns (rate, cores, seconds)."""
+    import multiprocessing as mp
+    from paper_2201_09212_gb300 import shard
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    cores = max(1, min(cores, sc.n_nodes // (dims[0] * dims[1])))
+    ranges = shard.partition(sc.row_ptr, cores, align=dims[0] * dims[1])
+    jobs = []
+    for n0, n1 in ranges:
+        halo = shard.halo_of(sc.row_ptr, sc.col_idx, n0, n1)
+        r0, r1 = int(sc.row_ptr[n0]), int(sc.row_ptr[n1])
+        cols = sc.col_idx[r0:r1].astype(np.int64)
+        own = (cols >= n0) & (cols < n1)
+        local = np.where(own, cols - n0, (n1 - n0) + np.searchsorted(halo, cols))
+        nh = len(halo)
+        row_ptr = np.concatenate([sc.row_ptr[n0:n1 + 1] - r0, (r1 - r0) + np.arange(1, nh + 1)])
+        col_idx = np.concatenate([local, (n1 - n0) + np.arange(nh)])
+        vals = np.concatenate([sc.vals[r0:r1].astype(np.float64), np.broadcast_to(np.eye(3), (nh, 3, 3))])
+        b = np.concatenate([sc.b[3 * n0:3 * n1], np.zeros(3 * nh)])
+        cm = (sc.node_i >= n0) & (sc.node_i < n1)
+        v0 = np.concatenate([sc.v0[3 * n0:3 * n1], sc.v0.reshape(-1, 3)[halo].ravel()])
+        jobs.append({"problem": (row_ptr, col_idx, vals, b, sc.node_i[cm] - n0, sc.node_j[cm],
+                                 sc.R[cm], sc.mu[cm], sc.phi[cm]),
+                     "v0": v0, "sweeps": sweeps})
+    ctx = mp.get_context("spawn")   # this process already holds a CUDA context
+    start, results = ctx.Barrier(len(jobs)), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_block_worker, args=(j, start, results)) for j in jobs]
+    for p in procs:
+        p.start()
+    times = [results.get() for _ in procs]
+    for p in procs:
+        p.join()
+    t = max(times)
+    return sc.n * sweeps / t, len(jobs), t
 
 
 def run_reference(args, sc):
@@ -334,7 +412,11 @@ def batched_bench(args, torch, dev, stream, rank):
         "steps": args.batch_steps, "dof_iters_per_s": dof_iters / t_total,
         "iters_per_scene": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
         "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
-                         "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0]},
+                         "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0],
+                         "traffic_over_algorithmic": (
+                             NCU_BATCH_TRAFFIC[source_hash()][0] / NCU_BATCH_TRAFFIC[source_hash()][1]
+                             if source_hash() in NCU_BATCH_TRAFFIC and var < 16 and threads == 256
+                             else None)},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
         "layout": {"blocks": int(sc.nnzb), "stored_slots": int(lay_b["slots"]),
                    "padding": lay_b["slots"] / sc.nnzb - 1.0},
@@ -398,7 +480,10 @@ def configs_bench(args, torch, dev, stream):
                                     stream=stream) as s:
             v0 = torch.from_numpy(sc.v0).to(dev)
             s.set_velocity(v0)
-            tuned = tune.tune(s, sweeps=20, reps=2)
+            # under the timing loop's condition (L2 flushed before each solve),
+            # windows of 40 sweeps, best of 3
+            tuned = tune.tune(s, sweeps=40, reps=3, condition="l2-flushed",
+                              before_rep=lambda: flush.fill_(0.0))
             kms, its = [], []
             with torch.cuda.stream(stream):
                 for k in range(3 + steps):
@@ -420,6 +505,9 @@ def configs_bench(args, torch, dev, stream):
                      "matrix_mb": sc.nnzb * (9 * esz + 4) / 1e6,
                      "path": "grid" if lay["path"] == 1 else "CTA-per-scene",
                      "launch": {k: tuned[k] for k in ("kernel_variant", "block_threads", "grid")},
+                     "tuner_best": [[t["kernel_variant"], t["grid"], round(1e3 * t["ms_per_sweep"], 2)]
+                                    for t in sorted(tuned.get("trials", []),
+                                                    key=lambda t: t["ms_per_sweep"])[:5]],
                      "l2": "flushed between steps (256 MB write)"}
     return out
 
@@ -666,11 +754,18 @@ def main():
                 "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
                           + (" (symmetric storage; effective fraction)" if sym else ""),
                 "kernel_ms_avg": 1e3 * k_avg}
-    cpu = None
+    cpu = cpu_all = None
     if ws == 1 and not args.no_cpu_baseline:
         rate, cores, dt = cpu_oracle_rate(sc, args.cpu_sweeps)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_sweeps} FP64 oracle V-FPI sweeps of the full workload ({dt:.1f} s)"}
+               "sample": f"{args.cpu_sweeps} FP64 oracle V-FPI sweeps of the full workload ({dt:.1f} s)",
+               "cpu_model": cpu_model()}
+        rate, cores, dt = cpu_oracle_rate_all_cores(sc, dims, 4 * args.cpu_sweeps)
+        cpu_all = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": (f"{4 * args.cpu_sweeps} FP64 oracle V-FPI sweeps of each of {cores} "
+                              f"z-slabs of the full workload, one process per core, all at once "
+                              f"(slowest slab {dt:.1f} s; halo exchange not timed)"),
+                   "nproc": os.cpu_count(), "cpu_model": cpu_model()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -688,6 +783,7 @@ def main():
         "roofline": roofline,
         "time_to_solution": time_to_solution,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
