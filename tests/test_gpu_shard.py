@@ -141,3 +141,53 @@ def test_shard_entry_points_check_their_arguments(lattice):
     with pytest.raises(vfpi.VfpiError) as x:
         shard.shard_solver(sc, pl, chebyshev_ls=5)
     assert x.value.status == code["VFPI_ERR_UNSUPPORTED"]
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir, sweeps):
+    """One rank: its shard's library context on the GPU, the boundary rows
+    moved through host tensors over gloo (no kernel waits on another rank:
+    every exchange goes through the host between launches)."""
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        sc = scenes.terrain_lattice(dims=DIMS)
+        ranges = shard.partition(sc.row_ptr, world, align=DIMS[0] * DIMS[1])
+        plan = shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, rank)
+        with shard.shard_solver(sc, plan) as eng:
+            r = shard.solve(eng, plan, shard.TorchComm(dist, "cpu"),
+                            sc.v0[3 * plan.n0:3 * plan.n1], n_dof=sc.n, theta_th=0.0,
+                            l_max=sweeps, norm="abs", device="cpu")
+            lam = np.asarray(eng.get_lambda())
+        np.savez(f"{out_dir}/r{rank}.npz", v=np.asarray(r.v), lam=lam, iters=r.iters,
+                 theta=r.theta, contacts=plan.contacts)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_processes_over_gloo_equal_the_unsplit_solve(lattice, tmp_path):
+    """shard.solve over torch.distributed with the library's shard contexts:
+    two ranks (processes) on this GPU, the unsplit solve's iterate and
+    impulses bit for bit after 12 sweeps."""
+    import torch.multiprocessing as mp
+    sweeps = 12
+    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path), sweeps), nprocs=2,
+                       start_method="spawn")
+    sc = lattice
+    with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=sweeps) as s:
+        ref = s.solve(sc.v0)
+    got = [np.load(tmp_path / f"r{r}.npz") for r in range(2)]
+    assert all(int(g["iters"]) == sweeps for g in got)
+    assert float(got[0]["theta"]) == float(got[1]["theta"])
+    assert np.array_equal(np.concatenate([g["v"] for g in got]), ref.v)
+    lam = np.full((sc.n_c, 3), np.nan, dtype=np.float32)
+    for g in got:
+        lam[g["contacts"]] = g["lam"].reshape(-1, 3)
+    assert np.array_equal(lam, np.asarray(ref.lam).reshape(-1, 3))
