@@ -145,3 +145,28 @@ def test_scene_path_times_whole_solves_and_restores_the_warm_start():
     # cluster shapes at 2.98 ms are inside the 2 % margin of 3.0 ms: the plain 256
     assert (r["kernel_variant"], r["block_threads"]) == (0, 256)
     assert np.array_equal(s.get_velocity(), v_start) and s.tol == (1e-6, 200)
+
+
+def test_hook_runs_before_every_timed_launch_and_keys_the_cache(tmp_path):
+    """A hook (the benchmark flushes L2 there) runs before each timed launch,
+    so the ranking is taken under the condition the solves will meet; results
+    under a named condition are cached apart from the plain ones."""
+    seen = []
+
+    class Flushing(FakeSolver):
+        def solve_async(self):
+            seen.append(("launch", self.shape))
+            super().solve_async()
+
+    s = Flushing(1, grid_cost(1.0), refuse=range(12, 16))
+    r = tune.tune(s, sweeps=10, reps=2, cache=str(tmp_path / "t.json"),
+                  before_rep=lambda: seen.append(("hook", None)), condition="l2-flushed")
+    launches = [i for i, e in enumerate(seen) if e[0] == "launch"]
+    assert launches and all(seen[i - 1][0] == "hook" for i in launches)
+    assert sum(e[0] == "hook" for e in seen) == len(launches) == 2 * len(r["trials"])
+    table = json.load(open(tmp_path / "t.json"))
+    assert len(table) == 1 and next(iter(table)).endswith("|l2-flushed")
+    # a plain tuning of the same layout does not reuse the flushed result
+    again = tune.tune(FakeSolver(1, grid_cost(1.0), refuse=range(12, 16)), sweeps=10, reps=1,
+                      cache=str(tmp_path / "t.json"))
+    assert not again["cached"] and len(json.load(open(tmp_path / "t.json"))) == 2
