@@ -404,7 +404,8 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
  * own nodes); a column index c < n_nodes is own node c, c >= n_nodes is halo
  * node c - n_nodes.  A row's columns need not increase (keep the unsplit
  * scene's order and the row sums are bit for bit those of the unsplit scene)
- * but each appears once, the diagonal block included.  Contacts join own nodes
+ * but each appears once, the diagonal block included (so a row holds 1 to
+ * n_nodes + n_halo blocks).  Contacts join own nodes
  * only (a contact across shards gives VFPI_ERR_INVALID_ARG).  A shard runs on
  * the grid path (full storage), without Chebyshev, Barzilai-Borwein steps,
  * the adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).

@@ -622,7 +622,10 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   }
   for (int i = 0; i < N; ++i) {
     const int len = row_ptr[i + 1] - row_ptr[i];
-    if (len < 1 || len > N) { c->err = "row_ptr: every row needs 1..n_nodes blocks"; return fail(VFPI_ERR_INVALID_ARG); }
+    if (len < 1 || len > N + c->n_halo) {
+      c->err = "row_ptr: every row needs 1..n_nodes (+ n_halo) blocks";
+      return fail(VFPI_ERR_INVALID_ARG);
+    }
   }
   auto row_len = [&](int i) { return row_ptr[i + 1] - row_ptr[i]; };
 

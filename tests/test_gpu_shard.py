@@ -191,3 +191,43 @@ def test_two_processes_over_gloo_equal_the_unsplit_solve(lattice, tmp_path):
     for g in got:
         lam[g["contacts"]] = g["lam"].reshape(-1, 3)
     assert np.array_equal(lam, np.asarray(ref.lam).reshape(-1, 3))
+
+
+def test_shards_with_d_contacts_in_fp64_equal_the_unsplit_solve():
+    """FP64, a random SPD problem with S- and D-contacts (the D-contact phase
+    and its mid-sweep barrier run on every shard), each D-contact inside one
+    shard: bitwise the unsplit solve after 1 and 9 sweeps, and at convergence
+    within FP64 rounding of the oracle."""
+    import dataclasses
+    rng = np.random.default_rng(7)
+    sc = scenes.random_problem(rng, 300, 40, d_contacts=40, density=0.03, couple=0.4)
+    ranges = shard.partition(sc.row_ptr, 2)
+    cut = ranges[0][1]
+    keep = (sc.node_j < 0) | ((sc.node_i < cut) == (sc.node_j < cut))
+    sc = dataclasses.replace(sc, node_i=sc.node_i[keep], node_j=sc.node_j[keep], R=sc.R[keep],
+                             mu=sc.mu[keep], phi=sc.phi[keep])
+    assert (sc.node_j >= 0).sum() >= 10
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(2)]
+    assert all((pl.node_j >= 0).any() for pl in plans)
+    engines = [shard.shard_solver(sc, pl, dtype="f64") for pl in plans]
+    try:
+        for sweeps in (1, 9):
+            with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=sweeps, force_path=1) as s:
+                ref = s.solve(sc.v0)
+            r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
+                                  dtype=torch.float64, device="cuda")
+            assert np.array_equal(r.v, ref.v), sweeps
+            lam = np.full((sc.n_c, 3), np.nan)
+            for e, pl in zip(engines, plans):
+                lam[pl.contacts] = np.asarray(e.get_lambda()).reshape(-1, 3)
+            assert np.array_equal(lam, np.asarray(ref.lam).reshape(-1, 3)), sweeps
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=1e-12, l_max=20000,
+                              dtype=torch.float64, device="cuda")
+    finally:
+        for e in engines:
+            e.close()
+    assert r.status == vfpi.VFPI_OK
+    P = oracle_problem(sc)
+    ref = ov.solve(P, ov.frobenius_w(P), sc.v0, theta_th=1e-13, l_max=200000)
+    assert np.linalg.norm(r.v - ref.v) <= 1e-9 * np.linalg.norm(ref.v)
