@@ -405,10 +405,12 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
  * node c - n_nodes.  A row's columns need not increase (keep the unsplit
  * scene's order and the row sums are bit for bit those of the unsplit scene)
  * but each appears once, the diagonal block included (so a row holds 1 to
- * n_nodes + n_halo blocks).  Contacts join own nodes
- * only (a contact across shards gives VFPI_ERR_INVALID_ARG).  A shard runs on
- * the grid path (full storage), without Chebyshev, Barzilai-Borwein steps,
- * the adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).
+ * n_nodes + n_halo blocks).  A contact joins own nodes, except that one node
+ * of a D-contact may be a halo node (a "split" contact: the other shard holds
+ * it too, with the roles of the nodes unchanged); an S-contact on a halo node,
+ * or a D-contact between two halo nodes, gives VFPI_ERR_INVALID_ARG.  A shard
+ * runs on the grid path (full storage), without Chebyshev, Barzilai-Borwein
+ * steps, the adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).
  *
  * A sweep of the whole scene is then: every shard calls vfpi_shard_sweep; the
  * callers sum the shards' sumsq (theta^2 of Alg. 1 = the sum; rms: / n of the
@@ -416,12 +418,31 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
  * neighbours need with vfpi_get_nodes and sets the rows it receives with
  * vfpi_set_halo.  The package's shard module drives this over
  * torch.distributed (NCCL between GPUs); nothing here communicates.
+ *
+ * Split contacts.  The step of a D-contact (Alg. 2) needs v* (eq. pgd1) of
+ * both nodes, so on a shard with split contacts a sweep has a second half:
+ * after vfpi_shard_sweep, the shard gives the v* of its own endpoints
+ * (vfpi_get_split_vstar), receives the other endpoints' v* from their shards,
+ * and vfpi_finish_split takes each contact's step and eq. (vup) for its own
+ * endpoint.  Both shards of a split contact take the step from the same
+ * inputs, so both get the same lambda and each node the unsplit solve's
+ * v^{l+1}.  The Frobenius-norm W (Sec. IV.C) is tied over a D-contact's two
+ * nodes and formed from both nodes' row statistics: before the first sweep
+ * (and after vfpi_update), each shard exchanges those of its endpoints
+ * (vfpi_get_split_stats, vfpi_set_split_stats).  Split contacts are counted
+ * and ordered as the caller's contact list orders them (k = 0..n_split-1);
+ * arrays below are indexed by that k.
  * ---------------------------------------------------------------------- */
 
+/* info2[0] = n_halo, info2[1] = n_split (the split contacts). */
+vfpi_status vfpi_get_shard_info(vfpi_t ctx, int32_t* info2);
+
 /* One sweep (eq. pgd1, Alg. 2, eq. vup) of this shard's rows from its current
- * iterate and the halo values last set; the iterate advances.  sumsq_out
- * (host double, nullable): this shard's FP64 sum of ||v^{l+1} - v^l||^2 over
- * its rows, in a fixed order.  Synchronises the stream when sumsq_out is set. */
+ * iterate and the halo values last set; the iterate advances (the own
+ * endpoints of split contacts stay at v^l until vfpi_finish_split).
+ * sumsq_out (host double, nullable): this shard's FP64 sum of
+ * ||v^{l+1} - v^l||^2 over its rows (without the own endpoints of split
+ * contacts), in a fixed order.  Synchronises the stream when sumsq_out is set. */
 vfpi_status vfpi_shard_sweep(vfpi_t ctx, double* sumsq_out);
 /* Copy the current v of own nodes nodes[0..n) (indices < n_nodes, host or
  * device array) into out [3n] (host or device).  An index out of range gives
@@ -430,6 +451,29 @@ vfpi_status vfpi_get_nodes(vfpi_t ctx, const int32_t* nodes, int32_t n, void* ou
 /* Set the v of halo nodes [first, first + n) from vals [3n] (host or device);
  * 0 <= first, first + n <= n_halo. */
 vfpi_status vfpi_set_halo(vfpi_t ctx, int32_t first, int32_t n, const void* vals);
+/* out [6 n_split] (host or device double): for split contact k, the row
+ * statistics of its own endpoint -- a_rr of its three DOFs, then ||A_r*||^2 of
+ * the three (FP64, the terms of the Frobenius W) -- of the current A. */
+vfpi_status vfpi_get_split_stats(vfpi_t ctx, double* out);
+/* partner [6 n_split] (host or device double): the other endpoints'
+ * statistics, as their shards' vfpi_get_split_stats gave them.  With
+ * VFPI_W_FROBENIUS, W is formed again; other W modes do not use them.  Until
+ * this call (after vfpi_create, vfpi_update), vfpi_shard_sweep with split
+ * contacts and VFPI_W_FROBENIUS gives VFPI_ERR_INVALID_ARG.  Non-finite
+ * values give VFPI_ERR_NONFINITE. */
+vfpi_status vfpi_set_split_stats(vfpi_t ctx, const double* partner);
+/* out [3 n_split] (host or device, the context's dtype): v* of each split
+ * contact's own endpoint, from the last vfpi_shard_sweep. */
+vfpi_status vfpi_get_split_vstar(vfpi_t ctx, void* out);
+/* Second half of a shard sweep: partner_vstar [3 n_split] (host or device,
+ * the context's dtype) holds the other endpoints' v*; each split contact's
+ * step (Alg. 2 with gamma = w_i + w_j, eq. diagonal) gives lambda and its own
+ * endpoint's v^{l+1} (eq. vup).  sumsq_out (host double, nullable): this
+ * shard's whole FP64 ||v^{l+1} - v^l||^2 of the sweep (vfpi_shard_sweep's sum,
+ * which leaves out the own endpoints of split contacts, plus theirs);
+ * synchronises the stream when set.  With no split contacts it only reads the
+ * sum. */
+vfpi_status vfpi_finish_split(vfpi_t ctx, const void* partner_vstar, double* sumsq_out);
 
 /* Message for the last failing vfpi_solve_noalloc call of this host thread. */
 const char* vfpi_noalloc_last_error(void);

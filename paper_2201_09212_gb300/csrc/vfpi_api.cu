@@ -2,6 +2,7 @@
 // staging, layout set-up, contact bookkeeping and dispatch to the per-dtype
 // launchers.  Host code only; every step of the solve runs in the kernels.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -127,7 +128,7 @@ void free_all(vfpi_ctx* c) {
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
                   c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
                   c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos,
-                  c->d_thscene, c->d_slicesq, c->d_sumsq};
+                  c->d_thscene, c->d_slicesq, c->d_sumsq, c->d_split_cs, c->d_split_own};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -232,13 +233,17 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
       else phi[k - 10 * (size_t)n_c] = v;
     }
   }
-  // validation
-  std::vector<int32_t> owner(c->N, -1);
+  // validation (a shard's D-contact may have one node in the halo: a split contact)
+  const int NH = c->N + c->n_halo;
+  std::vector<int32_t> owner(NH, -1);
   for (int m = 0; m < n_c; ++m) {
     const int i = ni[m], j = nj[m];
-    if (i < 0 || i >= c->N || j < -1 || j >= c->N || i == j)
+    if (i < 0 || i >= NH || j < -1 || j >= NH || i == j)
       return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": node index out of range");
-    if (j >= 0 && c->h_node_scene[i] != c->h_node_scene[j])
+    if (i >= c->N && (j < 0 || j >= c->N))
+      return arg_fail(c, VFPI_ERR_INVALID_ARG,
+                      "contact " + std::to_string(m) + ": a halo node only as one end of a D-contact");
+    if (j >= 0 && i < c->N && j < c->N && c->h_node_scene[i] != c->h_node_scene[j])
       return arg_fail(c, VFPI_ERR_INVALID_ARG, "contact " + std::to_string(m) + ": D-contact across scenes");
     for (int q : {i, j}) {
       if (q < 0) continue;
@@ -275,6 +280,7 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   c->h_ci.assign(n_c, -1);
   c->h_cj.assign(n_c, -1);
   std::vector<int32_t> cslot(c->n_pad, -1), dlist;
+  std::vector<std::array<int32_t, 3>> split;   // (caller index, internal contact, own row)
   std::vector<int32_t> scene_d(c->n_scenes + 1, 0);
   std::vector<unsigned char> Rint(c->esz * 9 * (size_t)n_c), muint(c->esz * (size_t)n_c),
       phint(c->esz * (size_t)n_c);
@@ -288,22 +294,35 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
     const int pj = nj[e] >= 0 ? c->h_node_map[nj[e]] : -1;
     c->h_ci[m] = pi;
     c->h_cj[m] = pj;
-    cslot[pi] = m;
+    if (pi < c->n_pad) cslot[pi] = m;
     if (pj >= 0) {
-      cslot[pj] = m;
-      dlist.push_back(m);
-      scene_d[c->h_node_scene[ni[e]] + 1]++;
+      if (pj < c->n_pad) cslot[pj] = m;
+      if (pi >= c->n_pad || pj >= c->n_pad) {
+        split.push_back({e, m, pi < c->n_pad ? pi : pj});
+      } else {
+        dlist.push_back(m);
+        scene_d[c->h_node_scene[ni[e]] + 1]++;
+      }
     }
     for (int q = 0; q < 9; ++q) put(Rint, (size_t)q * n_c + m, R[9 * (size_t)e + q]);
     put(muint, m, mu[e]);
     put(phint, m, phi[e]);
   }
   for (int q = 0; q < c->n_scenes; ++q) scene_d[q + 1] += scene_d[q];
+  // split contacts in the caller's order (both shards of a contact list them alike)
+  std::sort(split.begin(), split.end());
+  std::vector<int32_t> split_cs(split.size()), split_own(split.size());
+  for (size_t k = 0; k < split.size(); ++k) {
+    split_cs[k] = split[k][1];
+    split_own[k] = split[k][2];
+  }
   // (re)allocate contact arrays once earlier work on the stream has finished
   VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
   c->n_c = n_c;
   c->n_d = (int)dlist.size();
-  int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist};
+  c->n_split = (int)split.size();
+  c->split_ready = 0;
+  int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_split_cs, c->d_split_own};
   for (auto p : ip) if (p) cudaFree(p);
   void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2, c->d_lam, c->d_lam_star,
                 c->d_dstar};
@@ -312,6 +331,8 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(dalloc(&c->d_cj, 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cperm, 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_dlist, 4 * dlist.size()));
+  VFPI_TRY_CUDA(dalloc(&c->d_split_cs, 4 * split.size()));
+  VFPI_TRY_CUDA(dalloc(&c->d_split_own, 4 * split.size()));
   VFPI_TRY_CUDA(dalloc(&c->d_cR, c->esz * 9 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cmu, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cphi, c->esz * (size_t)n_c));
@@ -325,6 +346,10 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cj, c->h_cj.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cperm, perm.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_dlist, dlist.data(), 4 * dlist.size(), cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_split_cs, split_cs.data(), 4 * split.size(),
+                                cudaMemcpyHostToDevice, st));
+  VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_split_own, split_own.data(), 4 * split.size(),
+                                cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cR, Rint.data(), Rint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_cmu2, muint.data(), muint.size(), cudaMemcpyHostToDevice, st));
@@ -351,13 +376,15 @@ vfpi_status set_w(vfpi_ctx* c) {
                                   : (double)reinterpret_cast<const float*>(raw.data())[k];
     };
     // Prop. 3: the three entries of a contact node (six of a D-contact) are tied
+    // (on a shard, over the own endpoint of a split contact: the other shard
+    // checks the other one)
     std::vector<int32_t> inv(c->n_pad, -1);
     for (int i = 0; i < c->N; ++i) inv[c->h_node_map[i]] = i;
     for (int m = 0; m < c->n_c; ++m) {
-      const int i = inv[c->h_ci[m]];
+      const int i = inv[c->h_ci[m] < c->n_pad ? c->h_ci[m] : c->h_cj[m]];
       const double w0 = wv(3 * (size_t)i);
       for (int node : {c->h_ci[m], c->h_cj[m]}) {
-        if (node < 0) continue;
+        if (node < 0 || node >= c->n_pad) continue;
         const int e = inv[node];
         for (int a = 0; a < 3; ++a)
           if (wv(3 * (size_t)e + a) != w0)
@@ -707,7 +734,8 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_CUDA(dalloc(&c->d_sumsq, 8));
   CREATE_CUDA(dalloc(&c->d_row_ptr, 4 * ((size_t)N + 1)));
   CREATE_CUDA(cudaMemcpyAsync(c->d_row_ptr, row_ptr.data(), 4 * ((size_t)N + 1), cudaMemcpyHostToDevice, c->stream));
-  CREATE_CUDA(dalloc(&c->d_ds, 8 * 6 * (size_t)c->n_pad));
+  CREATE_CUDA(dalloc(&c->d_ds, 8 * 6 * ((size_t)c->n_pad + c->n_halo)));
+  CREATE_CUDA(cudaMemsetAsync(c->d_ds, 0, 8 * 6 * ((size_t)c->n_pad + c->n_halo), c->stream));
   CREATE_CUDA(dalloc(&c->d_scene_slice, 4 * ((size_t)c->n_scenes + 1)));
   CREATE_CUDA(dalloc(&c->d_scene_d, 4 * ((size_t)c->n_scenes + 1)));
   CREATE_CUDA(dalloc(&c->d_order, 4 * (size_t)c->n_scenes));
@@ -839,6 +867,7 @@ vfpi_status vfpi_update(vfpi_t c, const void* A_vals, const void* b, const vfpi_
   vfpi_status st;
   if (A_vals) {
     if ((st = set_values(c, c->d_row_ptr, nullptr, A_vals, false, 0)) != VFPI_OK) return st;
+    c->split_ready = 0;   // the other shards' rows changed too: exchange their statistics again
   }
   if (Jc) {
     if ((st = set_contacts(c, Jc)) != VFPI_OK) return st;
@@ -1058,6 +1087,9 @@ vfpi_status vfpi_step(vfpi_t c, double* theta_out) {
 vfpi_status vfpi_shard_sweep(vfpi_t c, double* sumsq_out) {
   CTX_CHECK(c);
   if (c->path != 1) return arg_fail(c, VFPI_ERR_UNSUPPORTED, "shard sweeps run on the grid path");
+  if (c->n_split > 0 && c->opts.w_mode == VFPI_W_FROBENIUS && !c->split_ready)
+    return arg_fail(c, VFPI_ERR_INVALID_ARG,
+                    "split contacts: set the other endpoints' row statistics first (vfpi_set_split_stats)");
   // one sweep: l_max = 1, never "converged" early; the kernel leaves the
   // sweep's FP64 sum of squares in d_sumsq
   VFPI_TRY_CUDA(DISPATCH(c, solve(c, 1, -1.0, false)));
@@ -1099,6 +1131,71 @@ vfpi_status vfpi_set_halo(vfpi_t c, int32_t first, int32_t n, const void* vals) 
   const void* dv;
   VFPI_TRY_CUDA(device_view(c, vals, c->esz * 3 * (size_t)n, 0, &dv));
   VFPI_TRY_CUDA(DISPATCH(c, set_halo(c, first, n, dv)));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_shard_info(vfpi_t c, int32_t* info2) {
+  CTX_CHECK(c);
+  if (!info2) return arg_fail(c, VFPI_ERR_INVALID_ARG, "info is NULL");
+  info2[0] = c->n_halo;
+  info2[1] = c->n_split;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_split_stats(vfpi_t c, double* out) {
+  CTX_CHECK(c);
+  if (c->n_split == 0) return VFPI_OK;
+  if (!out) return arg_fail(c, VFPI_ERR_INVALID_ARG, "out is NULL");
+  const size_t bytes = 8 * 6 * (size_t)c->n_split;
+  void* dst;
+  VFPI_TRY_CUDA(out_view(c, out, bytes, 0, &dst));
+  // the Frobenius W keeps the statistics of the current A; other modes form them here
+  if (c->opts.w_mode != VFPI_W_FROBENIUS) VFPI_TRY_CUDA(DISPATCH(c, row_stats(c)));
+  VFPI_TRY_CUDA(DISPATCH(c, split_stats(c, static_cast<double*>(dst))));
+  if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_set_split_stats(vfpi_t c, const double* partner) {
+  CTX_CHECK(c);
+  if (c->n_split == 0) return VFPI_OK;
+  if (!partner) return arg_fail(c, VFPI_ERR_INVALID_ARG, "partner statistics are required");
+  const size_t bytes = 8 * 6 * (size_t)c->n_split;
+  std::vector<double> h(6 * (size_t)c->n_split);
+  VFPI_TRY_CUDA(to_host(h.data(), partner, bytes, c->stream));
+  for (double x : h)
+    if (!std::isfinite(x)) return arg_fail(c, VFPI_ERR_NONFINITE, "partner statistics not finite");
+  if (c->opts.w_mode != VFPI_W_FROBENIUS) return VFPI_OK;   // W does not use them
+  const void* dp;
+  VFPI_TRY_CUDA(device_view(c, partner, bytes, 0, &dp));
+  VFPI_TRY_CUDA(DISPATCH(c, split_set_stats(c, static_cast<const double*>(dp))));
+  c->split_ready = 1;
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_get_split_vstar(vfpi_t c, void* out) {
+  CTX_CHECK(c);
+  if (c->n_split == 0) return VFPI_OK;
+  if (!out) return arg_fail(c, VFPI_ERR_INVALID_ARG, "out is NULL");
+  const size_t bytes = c->esz * 3 * (size_t)c->n_split;
+  void* dst;
+  VFPI_TRY_CUDA(out_view(c, out, bytes, 0, &dst));
+  VFPI_TRY_CUDA(DISPATCH(c, split_vstar(c, dst)));
+  if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_finish_split(vfpi_t c, const void* partner_vstar, double* sumsq_out) {
+  CTX_CHECK(c);
+  if (c->n_split > 0) {
+    if (!partner_vstar) return arg_fail(c, VFPI_ERR_INVALID_ARG, "partner v* is required");
+    const void* dp;
+    VFPI_TRY_CUDA(device_view(c, partner_vstar, c->esz * 3 * (size_t)c->n_split, 0, &dp));
+    VFPI_TRY_CUDA(DISPATCH(c, split_finish(c, dp)));
+  }
+  if (!sumsq_out) return VFPI_OK;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(sumsq_out, c->d_sumsq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
   return VFPI_OK;
 }
 

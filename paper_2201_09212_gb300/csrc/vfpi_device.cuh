@@ -599,6 +599,9 @@ __device__ __forceinline__ double finish_row_core(const DevProblem<T>& P, int ro
     const int cj = __ldg(P.c_j + cs);
     if (cj >= 0) {  // D-contact: stage v* and finish in phase 2
       stv(P.dstar + 2 * cs + (row == cj ? 1 : 0), vn);
+      // a shard's split D-contact (other node in the halo) finishes after the
+      // launch, from the other shard's v*: carry v^l for its residual
+      if (cj >= P.n_pad || __ldg(P.c_i + cs) >= P.n_pad) stv(out, vo);
       return 0.0;
     }
     const ContactRec<T> c = load_contact(P, cs);
@@ -727,6 +730,24 @@ __device__ __forceinline__ double bb_d_contact(const DevProblem<T>& P, int cs, c
   return sqdiff(ni, ldv(vin + i)) + sqdiff(nj, ldv(vin + j));
 }
 
+// Alg. 2 for D-contact cs from the v* of its nodes (si at node i, sj at node
+// j) and their W: stores lambda and lambda*, returns both nodes' eq. (vup) values.
+template <typename T>
+__device__ __forceinline__ void d_contact_step(const DevProblem<T>& P, int cs, const Vec4<T>& si,
+                                               const Vec4<T>& sj, T wi, T wj, Vec4<T>& ni,
+                                               Vec4<T>& nj) {
+  const ContactRec<T> c = load_contact(P, cs);
+  const T gamma = wi + wj + c.omega;                       // eq. (diagonal), D-contact; eq. (invt)
+  Vec4<T> ls, lam;
+  one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam, P.aniso ? 2 : P.prox);
+  T dx, dy, dz;
+  rt_lambda(c, lam, dx, dy, dz);
+  ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
+  nj = {sj.x - wj * dx, sj.y - wj * dy, sj.z - wj * dz, T(0)};
+  stv(P.lam + cs, lam);
+  stv(P.lam_star + cs, ls);
+}
+
 // Phase 2: D-contact d between internal nodes i and j (both rows hold v*).
 template <typename T, bool ADJ>
 __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, const Vec4<T>* vin,
@@ -734,10 +755,10 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
   const int i = P.c_i[cs], j = P.c_j[cs];
   const Vec4<T> si = ldv(P.dstar + 2 * cs), sj = ldv(P.dstar + 2 * cs + 1);
   const T wi = P.w[i].x, wj = P.w[j].x;
-  const ContactRec<T> c = load_contact(P, cs);
-  const T gamma = wi + wj + c.omega;                       // eq. (diagonal), D-contact; eq. (invt)
   Vec4<T> ni, nj;
   if constexpr (ADJ) {
+    const ContactRec<T> c = load_contact(P, cs);
+    const T gamma = wi + wj + c.omega;
     Vec4<T> q;
     T gphi, gmu;
     adjoint_step(c, ldv(P.adj_ls + cs), gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, q, gphi, gmu,
@@ -750,14 +771,7 @@ __device__ __forceinline__ double d_contact(const DevProblem<T>& P, int cs, cons
     P.adj_gphi[cs] = gphi;
     P.adj_gmu[cs] = gmu;
   } else {
-    Vec4<T> ls, lam;
-    one_shot(c, gamma, si.x - sj.x, si.y - sj.y, si.z - sj.z, ls, lam, P.aniso ? 2 : P.prox);
-    T dx, dy, dz;
-    rt_lambda(c, lam, dx, dy, dz);
-    ni = {si.x + wi * dx, si.y + wi * dy, si.z + wi * dz, T(0)};
-    nj = {sj.x - wj * dx, sj.y - wj * dy, sj.z - wj * dz, T(0)};
-    stv(P.lam + cs, lam);
-    stv(P.lam_star + cs, ls);
+    d_contact_step(P, cs, si, sj, wi, wj, ni, nj);
   }
   const Vec4<T> oi = ldv(vin + i), oj = ldv(vin + j);
   ni = cheb_combine(ch, ni, oi, vout + i);
@@ -1947,6 +1961,83 @@ __global__ void k_set_halo(int n, int64_t base, const T* __restrict__ vals, Vec4
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   stv(v + base + k, Vec4<T>{vals[3 * (int64_t)k], vals[3 * (int64_t)k + 1], vals[3 * (int64_t)k + 2], T(0)});
+}
+
+// Split D-contacts of a shard: one node own, the other a halo node that
+// another shard owns.  Both shards hold the contact and take its step of
+// Alg. 2 from the same inputs -- their own endpoint's v*, the other endpoint's
+// v* received from the other shard, W (tied over the contact's two nodes,
+// Prop. 3) -- so they get the same lambda bit for bit, and each applies eq.
+// (vup) to its own endpoint.  k = 0..n-1 runs over the split contacts in the
+// caller's contact order; cs[k] is the internal contact, own[k] its own row.
+
+// out[6k + q]: the row statistics (a_rr, ||A_r*||^2 of the three DOFs) of the
+// own endpoint of split contact k.
+static __global__ void k_split_stats(int n, const int32_t* __restrict__ own,
+                                     const double* __restrict__ ds, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6 * n) return;
+  out[t] = ds[6 * (int64_t)own[t / 6] + t % 6];
+}
+
+// The other endpoint's statistics (from the other shard) into its halo slot of ds.
+static __global__ void k_split_set_stats(int n, const int32_t* __restrict__ cs,
+                                         const int32_t* __restrict__ own,
+                                         const int32_t* __restrict__ c_i,
+                                         const int32_t* __restrict__ c_j,
+                                         const double* __restrict__ partner,
+                                         double* __restrict__ ds) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6 * n) return;
+  const int k = t / 6, m = cs[k];
+  const int other = own[k] == c_i[m] ? c_j[m] : c_i[m];
+  ds[6 * (int64_t)other + t % 6] = partner[t];
+}
+
+// out[3k..3k+2]: v* (eq. pgd1) of the own endpoint of split contact k, as the
+// last shard sweep staged it.
+template <typename T>
+__global__ void k_split_vstar(int n, const int32_t* __restrict__ cs, const int32_t* __restrict__ own,
+                              const int32_t* __restrict__ c_j, const Vec4<T>* __restrict__ dstar,
+                              T* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int m = cs[k];
+  const Vec4<T> q = ldv(dstar + 2 * m + (own[k] == c_j[m] ? 1 : 0));
+  out[3 * (int64_t)k] = q.x;
+  out[3 * (int64_t)k + 1] = q.y;
+  out[3 * (int64_t)k + 2] = q.z;
+}
+
+// The step of each split contact from partner[3k..] (the other endpoint's
+// v*): the own endpoint's v^{l+1} into v0 (where the sweep left v^l), and
+// sumsq[0] += the FP64 sum of their ||v^{l+1} - v^l||^2, taken in a fixed
+// order by one CTA.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_split_finish(DevProblem<T> P, int n,
+                                                      const int32_t* __restrict__ cs,
+                                                      const int32_t* __restrict__ own,
+                                                      const T* __restrict__ partner,
+                                                      double* __restrict__ sumsq) {
+  __shared__ double red[33];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += NT) {
+    const int m = cs[k], r = own[k];
+    const bool at_j = r == P.c_j[m];
+    const Vec4<T> so = ldv(P.dstar + 2 * m + (at_j ? 1 : 0));
+    const Vec4<T> sp = {partner[3 * (int64_t)k], partner[3 * (int64_t)k + 1],
+                        partner[3 * (int64_t)k + 2], T(0)};
+    const T w = P.w[r].x;                      // tied: the same at both nodes
+    Vec4<T> ni, nj;
+    if (at_j) d_contact_step(P, m, sp, so, w, w, ni, nj);
+    else d_contact_step(P, m, so, sp, w, w, ni, nj);
+    const Vec4<T> nn = at_j ? nj : ni;
+    const Vec4<T> o = ldv(P.v0 + r);
+    stv(P.v0 + r, nn);
+    acc += sqdiff(nn, o);
+  }
+  acc = block_allreduce<NT>(acc, red);
+  if (threadIdx.x == 0) sumsq[0] += acc;
 }
 
 template <typename T>

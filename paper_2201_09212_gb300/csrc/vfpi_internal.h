@@ -22,10 +22,17 @@ struct Launch {
   // sharded scene: v of own nodes out, halo values in
   static cudaError_t gather_nodes(vfpi_ctx* c, const int32_t* nodes, int n, void* out);
   static cudaError_t set_halo(vfpi_ctx* c, int first, int n, const void* vals);
+  // split D-contacts (one node in the halo): own endpoints' row statistics
+  // out, the partner endpoints' in (then W again), own v* out, the contact step
+  static cudaError_t split_stats(vfpi_ctx* c, double* out);
+  static cudaError_t split_set_stats(vfpi_ctx* c, const double* partner);
+  static cudaError_t split_vstar(vfpi_ctx* c, void* out);
+  static cudaError_t split_finish(vfpi_ctx* c, const void* partner_vstar);
   static cudaError_t check_finite(const void* a, int64_t n, int* err, cudaStream_t s);
   static cudaError_t build_layout(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx,
                                   const void* vals, bool store_cols);
   static cudaError_t make_w(vfpi_ctx* c);
+  static cudaError_t row_stats(vfpi_ctx* c);
   static cudaError_t to_internal(vfpi_ctx* c, const void* ext, void* internal);
   static cudaError_t to_external(vfpi_ctx* c, const void* internal, void* ext);
   static cudaError_t lambda_external(vfpi_ctx* c, const void* lam_int, void* out);
@@ -55,6 +62,8 @@ struct vfpi_ctx {
   // sizes
   int N = 0, nnzb = 0, n_scenes = 1, n_slices = 0, n_pad = 0, n_c = 0, n_d = 0;
   int n_halo = 0;         // shard of a split scene: halo nodes, stored after the n_pad rows
+  int n_split = 0;        // shard: D-contacts with one node in the halo (split contacts)
+  int split_ready = 0;    // W_FROBENIUS: the split contacts' partner row statistics are set
   int64_t n_entries = 0;  // sum of slice lengths; stored block slots = 32 * n_entries
 
   // host copies of the layout and contact bookkeeping
@@ -82,7 +91,8 @@ struct vfpi_ctx {
   int32_t* d_cslot = nullptr;
   int32_t* d_node_map = nullptr;
   int32_t* d_row_ptr = nullptr;             // caller's row pointers (value updates)
-  double* d_ds = nullptr;                   // per-DOF row statistics for W
+  double* d_ds = nullptr;                   // per-DOF row statistics for W [n_pad + n_halo][6]
+  int32_t *d_split_cs = nullptr, *d_split_own = nullptr;  // [n_split] internal contact, own row
   int32_t *d_ci = nullptr, *d_cj = nullptr, *d_cperm = nullptr, *d_dlist = nullptr;
   void *d_cR = nullptr, *d_cmu = nullptr, *d_cphi = nullptr, *d_comega = nullptr;
   void* d_cmu2 = nullptr;                   // friction along t2 (elliptic cones)

@@ -138,6 +138,52 @@ cudaError_t Launch<T>::make_w(vfpi_ctx* c) {
 }
 
 template <typename T>
+cudaError_t Launch<T>::row_stats(vfpi_ctx* c) {
+  if (c->n_pad > 0)
+    k_row_stats<T><<<blocks_for(c->n_pad, 128), 128, 0, c->stream>>>(dev_problem<T>(c), c->d_ds);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::split_stats(vfpi_ctx* c, double* out) {
+  if (c->n_split > 0)
+    k_split_stats<<<blocks_for(6 * (int64_t)c->n_split, 256), 256, 0, c->stream>>>(
+        c->n_split, c->d_split_own, c->d_ds, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::split_set_stats(vfpi_ctx* c, const double* partner) {
+  cudaStream_t s = c->stream;
+  if (c->n_split == 0) return cudaSuccess;
+  k_split_set_stats<<<blocks_for(6 * (int64_t)c->n_split, 256), 256, 0, s>>>(
+      c->n_split, c->d_split_cs, c->d_split_own, c->d_ci, c->d_cj, partner, c->d_ds);
+  // W again from the row statistics (the own rows' are unchanged)
+  k_make_w_frobenius<T><<<blocks_for(c->n_pad, 256), 256, 0, s>>>(
+      c->n_pad, c->d_ds, c->d_cslot, c->d_ci, c->d_cj, static_cast<Vec4<T>*>(c->d_w));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::split_vstar(vfpi_ctx* c, void* out) {
+  if (c->n_split > 0)
+    k_split_vstar<T><<<blocks_for(c->n_split, 256), 256, 0, c->stream>>>(
+        c->n_split, c->d_split_cs, c->d_split_own, c->d_cj,
+        static_cast<const Vec4<T>*>(c->d_dstar), static_cast<T*>(out));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::split_finish(vfpi_ctx* c, const void* partner_vstar) {
+  if (c->n_split > 0)
+    k_split_finish<T, 256><<<1, 256, 0, c->stream>>>(dev_problem<T>(c), c->n_split, c->d_split_cs,
+                                                     c->d_split_own,
+                                                     static_cast<const T*>(partner_vstar),
+                                                     c->d_sumsq);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::to_internal(vfpi_ctx* c, const void* ext, void* internal) {
   if (c->N > 0)
     k_to_internal<T><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(

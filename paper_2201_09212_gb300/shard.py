@@ -8,17 +8,23 @@ scene is
 
 1. every shard sweeps its own rows (``vfpi_shard_sweep``), reading the latest
    v of its halo: the other shards' nodes that its rows reference;
-2. theta^2 of Alg. 1 is the sum of the shards' FP64 sums of squares, added in
+2. a D-contact whose nodes lie on two shards (a split contact) is held by
+   both: each sends the other the v* of its endpoint, and both take the
+   contact's step from the same inputs (``vfpi_finish_split``), each keeping
+   its own endpoint's update; the contact belongs to (its lambda is reported
+   by) the shard of its lower-numbered node;
+3. theta^2 of Alg. 1 is the sum of the shards' FP64 sums of squares, added in
    rank order on every rank (all take the same stop decision);
-3. unless the stop test ends the solve, each shard sends the rows its
+4. unless the stop test ends the solve, each shard sends the rows its
    neighbours need and sets the rows it receives as its halo.
 
-Contacts must join nodes of one shard (an S-contact always does).  The solve
-is plain Alg. 1 (the Chebyshev weights of Alg. 3 are not carried across the
-per-sweep launches).  This module is the host side only: the partition, the
-halo and send lists, the exchange over ``torch.distributed`` (NCCL between
-GPUs, gloo on CPUs) or inside one process, and the loop; every step of the
-sweep runs in the library's kernels.
+Before the first sweep the shards of each split contact also exchange the row
+statistics the tied Frobenius W of its two nodes is formed from (Sec. IV.C).
+The solve is plain Alg. 1 (the Chebyshev weights of Alg. 3 are not carried
+across the per-sweep launches).  This module is the host side only: the
+partition, the halo, send and split lists, the exchange over
+``torch.distributed`` (NCCL between GPUs, gloo on CPUs) or inside one process,
+and the loop; every step of the sweep runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -63,12 +69,16 @@ def halo_of(row_ptr, col_idx, n0: int, n1: int) -> np.ndarray:
 @dataclasses.dataclass
 class ShardPlan:
     """Everything one shard needs, in the shard's own numbering: own node
-    g -> g - n0, halo node halo[k] -> (n1 - n0) + k."""
+    g -> g - n0, halo node halo[k] -> (n1 - n0) + k.  The halo is first the
+    other shards' nodes that this shard's rows reference (sorted; exchanged
+    every sweep), then the other endpoints of split contacts that no row
+    references (sorted; only their v* is exchanged)."""
     rank: int
     ranges: list
     n0: int
     n1: int
-    halo: np.ndarray                 # global ids, sorted
+    halo: np.ndarray                 # global ids
+    n_halo_rows: int                 # the first part of the halo: referenced by rows
     row_ptr: np.ndarray              # [n_own + 1]
     col_idx: np.ndarray              # local numbering, the scene's column order
     blocks: slice                    # this shard's blocks in the scene's vals
@@ -77,6 +87,9 @@ class ShardPlan:
     node_j: np.ndarray               # local, -1 for S-contacts
     recv: dict                       # peer -> (first halo index, count)
     send: dict                       # peer -> local own ids the peer needs, in its halo order
+    split: np.ndarray                # positions in ``contacts`` of the split contacts
+    split_peer: dict                 # peer -> positions in ``split`` of the contacts shared with it
+    owns: np.ndarray                 # [len(contacts)] this shard reports the contact's lambda
 
     @property
     def n_own(self) -> int:
@@ -95,19 +108,43 @@ def make_plan(row_ptr, col_idx, node_i, node_j, ranges, rank: int) -> ShardPlan:
     node_j = (np.full(len(node_i), -1, dtype=np.int64) if node_j is None
               else np.asarray(node_j, dtype=np.int64))
     n0, n1 = ranges[rank]
-    halo = halo_of(row_ptr, col_idx, n0, n1)
+    inside = lambda g: (g >= n0) & (g < n1)                        # noqa: E731
+    halo_rows = halo_of(row_ptr, col_idx, n0, n1)
     cols = col_idx[row_ptr[n0]:row_ptr[n1]]
     own = (cols >= n0) & (cols < n1)
-    local = np.where(own, cols - n0, (n1 - n0) + np.searchsorted(halo, cols))
-    mine = (node_i >= n0) & (node_i < n1)
-    jm = node_j[mine]
-    if ((jm >= 0) & ((jm < n0) | (jm >= n1))).any():
-        raise ValueError("a contact joins nodes of two shards")
-    if ((node_j >= n0) & (node_j < n1) & ~mine).any():
-        raise ValueError("a contact joins nodes of two shards")
+    # this shard's contacts: every contact with a node here, in the scene's order
+    contacts = np.nonzero(inside(node_i) | inside(node_j))[0]
+    ci, cj = node_i[contacts], node_j[contacts]
+    is_split = (cj >= 0) & (inside(ci) != inside(cj))
+    other = np.where(inside(ci), cj, ci)[is_split]
+    extra = np.setdiff1d(other, halo_rows)
+    halo = np.concatenate([halo_rows, extra]).astype(np.int64)
+
+    def local_of(g):
+        """own g -> g - n0, halo g -> n_own + its halo position, -1 -> -1"""
+        g = np.asarray(g, dtype=np.int64)
+        if len(halo_rows):
+            k = np.minimum(np.searchsorted(halo_rows, g), len(halo_rows) - 1)
+            in_rows = halo_rows[k] == g
+        else:
+            k, in_rows = np.zeros(g.shape, np.int64), np.zeros(g.shape, bool)
+        hpos = np.where(in_rows, k, len(halo_rows) + np.searchsorted(extra, g))
+        out = np.where(inside(g), g - n0, (n1 - n0) + hpos)
+        return np.where(g < 0, -1, out).astype(np.int32)
+
+    local = np.where(own, cols - n0, (n1 - n0) + np.searchsorted(halo_rows, cols))
+    split = np.nonzero(is_split)[0]
+    split_peer = {}
+    if len(split):
+        peer_of = owner_of(ranges, other)
+        for p in np.unique(peer_of):
+            split_peer[int(p)] = np.nonzero(peer_of == p)[0]
+    # the contact belongs to the shard of its lower-numbered node
+    low = np.where(cj >= 0, np.minimum(ci, cj), ci)
+    owns = inside(low)
     recv = {}
-    if len(halo):
-        own_of = owner_of(ranges, halo)
+    if len(halo_rows):
+        own_of = owner_of(ranges, halo_rows)
         for p in np.unique(own_of):
             idx = np.nonzero(own_of == p)[0]
             recv[int(p)] = (int(idx[0]), int(len(idx)))
@@ -120,10 +157,11 @@ def make_plan(row_ptr, col_idx, node_i, node_j, ranges, rank: int) -> ShardPlan:
         if len(need):
             send[p] = (need - n0).astype(np.int32)
     return ShardPlan(rank=rank, ranges=list(ranges), n0=n0, n1=n1, halo=halo,
+                     n_halo_rows=len(halo_rows),
                      row_ptr=(row_ptr[n0:n1 + 1] - row_ptr[n0]).astype(np.int32),
                      col_idx=local.astype(np.int32), blocks=slice(int(row_ptr[n0]), int(row_ptr[n1])),
-                     contacts=np.nonzero(mine)[0], node_i=(node_i[mine] - n0).astype(np.int32),
-                     node_j=np.where(jm >= 0, jm - n0, -1).astype(np.int32), recv=recv, send=send)
+                     contacts=contacts, node_i=local_of(ci), node_j=local_of(cj), recv=recv,
+                     send=send, split=split, split_peer=split_peer, owns=owns)
 
 
 def shard_solver(scene, plan: ShardPlan, **kw) -> "vfpi.Solver":
@@ -209,6 +247,29 @@ def _set_halo(engine, plan, got):
         engine.set_halo(first, got[p])
 
 
+def _split_sends(plan, vals, width):
+    """Per peer: the rows (``width`` values each) of ``vals`` that belong to
+    the split contacts shared with it, in the split order."""
+    import torch
+    v = vals.view(-1, width)
+    return {p: v[torch.as_tensor(idx, device=v.device)].reshape(-1).contiguous()
+            for p, idx in plan.split_peer.items()}
+
+
+def _split_assemble(plan, got, width, like):
+    """The other endpoints' rows received from each peer, in the split order."""
+    import torch
+    out = torch.empty_like(like)
+    o = out.view(-1, width)
+    for p, idx in plan.split_peer.items():
+        o[torch.as_tensor(idx, device=o.device)] = got[p].view(-1, width)
+    return out
+
+
+def _split_shapes(plan, width):
+    return {p: width * len(idx) for p, idx in plan.split_peer.items()}
+
+
 def _theta(s2: float, n_dof: int, norm: str) -> float:
     th = math.sqrt(s2)
     return th / math.sqrt(n_dof) if norm == "rms" else th
@@ -231,12 +292,26 @@ def solve(engine, plan: ShardPlan, comm: TorchComm, v0_own, *, n_dof: int, theta
     dtype = dtype or torch.float32
     engine.set_velocity(v0_own)
     recv_shapes = {p: 3 * n for p, (_, n) in plan.recv.items()}
+    n_split = len(plan.split)
+    if n_split:    # the tied W of each split contact's two nodes
+        st = engine.split_stats(out=torch.empty(6 * n_split, dtype=torch.float64, device=device))
+        got = comm.exchange(_split_sends(plan, st, 6), _split_shapes(plan, 6), torch.float64)
+        engine.set_split_stats(_split_assemble(plan, got, 6, st))
     _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
                                           recv_shapes, dtype))
+
+    def sweep():
+        if not n_split:
+            return engine.shard_sweep()
+        engine.shard_sweep(sumsq=False)
+        vs = engine.split_vstar(out=torch.empty(3 * n_split, dtype=dtype, device=device))
+        got = comm.exchange(_split_sends(plan, vs, 3), _split_shapes(plan, 3), dtype)
+        return engine.finish_split(_split_assemble(plan, got, 3, vs))
+
     status = NOT_CONVERGED
     theta = float("nan")
     for l in range(1, l_max + 1):
-        s2 = comm.sum_in_rank_order(engine.shard_sweep())
+        s2 = comm.sum_in_rank_order(sweep())
         theta = _theta(s2, n_dof, norm)
         if not math.isfinite(theta):
             raise vfpi.VfpiError(vfpi.STATUS_CODES["VFPI_ERR_NONFINITE"], "non-finite residual")
@@ -265,15 +340,36 @@ def solve_local(engines, plans, v0, *, n_dof: int, theta_th: float, l_max: int,
         for e, pl in zip(engines, plans):
             _set_halo(e, pl, box.take(pl.rank, pl.recv))
 
+    def split_exchange(vals, width):
+        for pl, x in zip(plans, vals):
+            if len(pl.split):
+                box.post(pl.rank, _split_sends(pl, x, width))
+        return [_split_assemble(pl, box.take(pl.rank, pl.split_peer), width, x)
+                if len(pl.split) else None for pl, x in zip(plans, vals)]
+
+    split = any(len(pl.split) for pl in plans)
     for e, pl in zip(engines, plans):
         e.set_velocity(v0[3 * pl.n0:3 * pl.n1])
+    if split:
+        st = [e.split_stats(out=torch.empty(6 * len(pl.split), dtype=torch.float64, device=device))
+              for e, pl in zip(engines, plans)]
+        for e, x in zip(engines, split_exchange(st, 6)):
+            if x is not None:
+                e.set_split_stats(x)
     exchange()
     status = NOT_CONVERGED
     theta = float("nan")
     for l in range(1, l_max + 1):
+        parts = [e.shard_sweep(sumsq=not len(pl.split)) for e, pl in zip(engines, plans)]
+        if split:
+            vs = [e.split_vstar(out=torch.empty(3 * len(pl.split), dtype=dtype, device=device))
+                  for e, pl in zip(engines, plans)]
+            for k, (e, x) in enumerate(zip(engines, split_exchange(vs, 3))):
+                if x is not None:
+                    parts[k] = e.finish_split(x)
         s2 = 0.0
-        for e in engines:
-            s2 += e.shard_sweep()
+        for x in parts:
+            s2 += x
         theta = _theta(s2, n_dof, norm)
         if not math.isfinite(theta):
             raise vfpi.VfpiError(vfpi.STATUS_CODES["VFPI_ERR_NONFINITE"], "non-finite residual")

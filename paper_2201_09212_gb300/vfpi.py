@@ -38,7 +38,9 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
             "vfpi_set_barzilai_borwein",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
-            "vfpi_noalloc_last_error", "vfpi_shard_sweep", "vfpi_get_nodes", "vfpi_set_halo")
+            "vfpi_noalloc_last_error", "vfpi_shard_sweep", "vfpi_get_nodes", "vfpi_set_halo",
+            "vfpi_get_shard_info", "vfpi_get_split_stats", "vfpi_set_split_stats",
+            "vfpi_get_split_vstar", "vfpi_finish_split")
 
 
 class VfpiError(RuntimeError):
@@ -121,6 +123,11 @@ def lib():
         "vfpi_shard_sweep": (st, [vp, vp]),
         "vfpi_get_nodes": (st, [vp, vp, i32, vp]),
         "vfpi_set_halo": (st, [vp, i32, i32, vp]),
+        "vfpi_get_shard_info": (st, [vp, vp]),
+        "vfpi_get_split_stats": (st, [vp, vp]),
+        "vfpi_set_split_stats": (st, [vp, vp]),
+        "vfpi_get_split_vstar": (st, [vp, vp]),
+        "vfpi_finish_split": (st, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -300,11 +307,52 @@ class Solver:
         return iters, theta, st
 
     # ---------------------------------------------------------- sharded scene
-    def shard_sweep(self) -> float:
+    def shard_sweep(self, sumsq=True):
         """One sweep of this shard's rows (halo values as last set); returns the
-        shard's FP64 sum of squares of the update over its rows."""
+        shard's FP64 sum of squares of the update over its rows (without the
+        own endpoints of split contacts), or None, without waiting for the
+        GPU, when ``sumsq`` is false."""
+        if not sumsq:
+            self._check(self._L.vfpi_shard_sweep(self._h, None))
+            return None
         s2 = C.c_double()
         self._check(self._L.vfpi_shard_sweep(self._h, C.byref(s2)))
+        return float(s2.value)
+
+    def shard_info(self):
+        """(n_halo, n_split): halo nodes and split contacts (D-contacts with one
+        node in the halo) of this shard."""
+        info = np.zeros(2, dtype=np.int32)
+        self._check(self._L.vfpi_get_shard_info(self._h, info.ctypes.data))
+        return int(info[0]), int(info[1])
+
+    def split_stats(self, out=None):
+        """[6 n_split] FP64 row statistics (a_rr, ||A_r*||^2 of the three DOFs) of
+        each split contact's own endpoint."""
+        out = self._out(6 * self.shard_info()[1], out, np.float64)
+        k = _Keep()
+        self._check(self._L.vfpi_get_split_stats(self._h, k.ptr(out, np.float64)))
+        return out
+
+    def set_split_stats(self, partner):
+        """The other endpoints' statistics, [6 n_split] FP64 (W is formed again)."""
+        k = _Keep()
+        self._check(self._L.vfpi_set_split_stats(self._h, k.ptr(partner, np.float64)))
+
+    def split_vstar(self, out=None):
+        """[3 n_split] v* of each split contact's own endpoint, from the last sweep."""
+        out = self._out(3 * self.shard_info()[1], out)
+        k = _Keep()
+        self._check(self._L.vfpi_get_split_vstar(self._h, k.ptr(out, self.np_dtype)))
+        return out
+
+    def finish_split(self, partner_vstar) -> float:
+        """Second half of the sweep from the other endpoints' v* [3 n_split];
+        returns the shard's whole FP64 sum of squares of the sweep."""
+        s2 = C.c_double()
+        k = _Keep()
+        self._check(self._L.vfpi_finish_split(self._h, k.ptr(partner_vstar, self.np_dtype),
+                                              C.byref(s2)))
         return float(s2.value)
 
     def get_nodes(self, nodes, out=None):

@@ -37,10 +37,15 @@ def make_shards(sc, k, **kw):
     return plans, [shard.shard_solver(sc, pl, **kw) for pl in plans]
 
 
-def lambdas(engines, plans, n_c):
-    lam = np.full((n_c, 3), np.nan, dtype=np.float32)
+def lambdas(engines, plans, n_c, dtype=np.float32):
+    """The scene's lambda, each contact from the shard that owns it; a split
+    contact's other shard must hold the same lambda bit for bit."""
+    lam = np.full((n_c, 3), np.nan, dtype=dtype)
     for e, pl in zip(engines, plans):
-        lam[pl.contacts] = np.asarray(e.get_lambda()).reshape(-1, 3)
+        lam[pl.contacts[pl.owns]] = np.asarray(e.get_lambda()).reshape(-1, 3)[pl.owns]
+    for e, pl in zip(engines, plans):
+        mine = np.asarray(e.get_lambda()).reshape(-1, 3)
+        assert np.array_equal(mine, lam[pl.contacts])
     return lam
 
 
@@ -193,23 +198,75 @@ def test_two_processes_over_gloo_equal_the_unsplit_solve(lattice, tmp_path):
     assert np.array_equal(lam, np.asarray(ref.lam).reshape(-1, 3))
 
 
-def test_shards_with_d_contacts_in_fp64_equal_the_unsplit_solve():
-    """FP64, a random SPD problem with S- and D-contacts (the D-contact phase
-    and its mid-sweep barrier run on every shard), each D-contact inside one
-    shard: bitwise the unsplit solve after 1 and 9 sweeps, and at convergence
-    within FP64 rounding of the oracle."""
+def with_split_d_contacts(sc, ranges, n_per_cut=40, seed=11):
+    """The lattice plus D-contacts across each cut: node a within three layers
+    below the cut, node b within three layers above (some pairs coupled in A,
+    most not, so the other endpoint is a row-halo node or an extra halo node),
+    no node in two contacts, none on the contact layer."""
     import dataclasses
+    rng = np.random.default_rng(seed)
+    layer = DIMS[0] * DIMS[1]
+    used = set(int(x) for x in sc.node_i)
+    ni, nj = [], []
+    for c in (r[0] for r in ranges[1:]):
+        k = 0
+        while k < n_per_cut:
+            a = int(rng.integers(max(c - 3 * layer, layer), c))
+            b = int(rng.integers(c, min(c + 3 * layer, sc.n_nodes)))
+            if a in used or b in used:
+                continue
+            used.update((a, b))
+            # half of them with the lower node as node j
+            ni.append(a if k % 2 else b)
+            nj.append(b if k % 2 else a)
+            k += 1
+    m = len(ni)
+    R = scenes.random_rotations(rng, m).astype(sc.R.dtype)
+    return dataclasses.replace(
+        sc, node_i=np.concatenate([sc.node_i, ni]).astype(np.int32),
+        node_j=np.concatenate([sc.node_j, nj]).astype(np.int32),
+        R=np.concatenate([sc.R, R]), mu=np.concatenate([sc.mu, rng.uniform(0.2, 0.8, m)]).astype(sc.mu.dtype),
+        phi=np.concatenate([sc.phi, rng.uniform(-0.05, 0.02, m)]).astype(sc.phi.dtype))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_split_d_contacts_equal_the_unsplit_solve_bitwise(lattice, k):
+    """FP32 lattice with D-contacts across the cuts (v* exchanged mid-sweep,
+    row statistics before the first): iterate and impulses bit for bit the
+    unsplit solve's after 1, 7 and 30 sweeps."""
+    ranges = shard.partition(lattice.row_ptr, k, align=DIMS[0] * DIMS[1])
+    sc = with_split_d_contacts(lattice, ranges)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(k)]
+    engines = [shard.shard_solver(sc, pl) for pl in plans]
+    try:
+        for e, pl in zip(engines, plans):
+            assert e.shard_info() == (len(pl.halo), len(pl.split)) and len(pl.split) >= 40
+            assert len(pl.halo) > pl.n_halo_rows          # endpoints no row references
+        for sweeps in (1, 7, 30):
+            with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=sweeps, force_path=1) as s:
+                ref = s.solve(sc.v0)
+            r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
+                                  device="cuda")
+            assert np.array_equal(r.v, ref.v), sweeps
+            assert np.array_equal(lambdas(engines, plans, sc.n_c), np.asarray(ref.lam).reshape(-1, 3))
+            assert abs(r.theta - ref.theta) <= 1e-12 * ref.theta
+    finally:
+        for e in engines:
+            e.close()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_split_d_contacts_in_fp64_against_the_oracle(k):
+    """FP64, a random SPD problem whose D-contacts pair random nodes (about
+    half cross a cut): bitwise the unsplit solve after 1 and 9 sweeps, and at
+    convergence within FP64 rounding of the oracle."""
     rng = np.random.default_rng(7)
     sc = scenes.random_problem(rng, 300, 40, d_contacts=40, density=0.03, couple=0.4)
-    ranges = shard.partition(sc.row_ptr, 2)
-    cut = ranges[0][1]
-    keep = (sc.node_j < 0) | ((sc.node_i < cut) == (sc.node_j < cut))
-    sc = dataclasses.replace(sc, node_i=sc.node_i[keep], node_j=sc.node_j[keep], R=sc.R[keep],
-                             mu=sc.mu[keep], phi=sc.phi[keep])
-    assert (sc.node_j >= 0).sum() >= 10
+    ranges = shard.partition(sc.row_ptr, k)
     plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
-             for r in range(2)]
-    assert all((pl.node_j >= 0).any() for pl in plans)
+             for r in range(k)]
+    assert all(len(pl.split) >= 5 for pl in plans)
     engines = [shard.shard_solver(sc, pl, dtype="f64") for pl in plans]
     try:
         for sweeps in (1, 9):
@@ -218,12 +275,11 @@ def test_shards_with_d_contacts_in_fp64_equal_the_unsplit_solve():
             r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
                                   dtype=torch.float64, device="cuda")
             assert np.array_equal(r.v, ref.v), sweeps
-            lam = np.full((sc.n_c, 3), np.nan)
-            for e, pl in zip(engines, plans):
-                lam[pl.contacts] = np.asarray(e.get_lambda()).reshape(-1, 3)
+            lam = lambdas(engines, plans, sc.n_c, np.float64)
             assert np.array_equal(lam, np.asarray(ref.lam).reshape(-1, 3)), sweeps
         r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=1e-12, l_max=20000,
                               dtype=torch.float64, device="cuda")
+        lam = lambdas(engines, plans, sc.n_c, np.float64)
     finally:
         for e in engines:
             e.close()
@@ -231,3 +287,44 @@ def test_shards_with_d_contacts_in_fp64_equal_the_unsplit_solve():
     P = oracle_problem(sc)
     ref = ov.solve(P, ov.frobenius_w(P), sc.v0, theta_th=1e-13, l_max=200000)
     assert np.linalg.norm(r.v - ref.v) <= 1e-9 * np.linalg.norm(ref.v)
+    assert scc_residual(P, r.v, lam) <= 1e-9
+
+
+def test_split_contact_calls_check_their_arguments():
+    rng = np.random.default_rng(7)
+    sc = scenes.random_problem(rng, 120, 10, d_contacts=20, density=0.05, couple=0.4)
+    ranges = shard.partition(sc.row_ptr, 2)
+    pl = shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, 0)
+    code = vfpi.STATUS_CODES
+    n_split = len(pl.split)
+    assert n_split > 0
+    with shard.shard_solver(sc, pl, dtype="f64") as e:
+        # the tied W needs the other endpoints' statistics before a sweep
+        with pytest.raises(vfpi.VfpiError) as x:
+            e.shard_sweep()
+        assert x.value.status == code["VFPI_ERR_INVALID_ARG"]
+        bad = np.ones(6 * n_split)
+        bad[3] = np.inf
+        with pytest.raises(vfpi.VfpiError) as x:
+            e.set_split_stats(bad)
+        assert x.value.status == code["VFPI_ERR_NONFINITE"]
+        st = e.split_stats()
+        assert st.shape == (6 * n_split,) and (st[0::6] > 0).all()
+        e.set_split_stats(st)                     # any finite statistics are taken
+        e.set_velocity(sc.v0[3 * pl.n0:3 * pl.n1])
+        e.shard_sweep()
+        # the own endpoints stay at v^l until the second half of the sweep
+        own = np.where(pl.node_i[pl.split] < pl.n_own, pl.node_i[pl.split], pl.node_j[pl.split])
+        v = np.asarray(e.get_velocity()).reshape(-1, 3)
+        assert np.array_equal(v[own], sc.v0.reshape(-1, 3)[pl.n0 + own])
+        assert e.split_vstar().shape == (3 * n_split,)
+        e.finish_split(e.split_vstar())
+        assert not np.array_equal(np.asarray(e.get_velocity()).reshape(-1, 3)[own],
+                                  sc.v0.reshape(-1, 3)[pl.n0 + own])
+    # an S-contact on a halo node, a D-contact between two halo nodes
+    for ni, nj in ((pl.n_own, -1), (pl.n_own, pl.n_own + 1)):
+        with pytest.raises(vfpi.VfpiError) as x:
+            vfpi.Solver(pl.row_ptr, pl.col_idx, sc.vals[pl.blocks], sc.b[3 * pl.n0:3 * pl.n1],
+                        np.array([ni], np.int32), np.array([nj], np.int32), sc.R[:1], sc.mu[:1],
+                        sc.phi[:1], dtype="f64", n_halo=len(pl.halo))
+        assert x.value.status == code["VFPI_ERR_INVALID_ARG"]

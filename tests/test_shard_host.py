@@ -4,9 +4,12 @@ exchange and theta assembly, run over gloo ranks (world size 2 and 3) and in
 one process.  The sweep itself is played by a stand-in engine that runs the
 FP64 oracle's sweep (Alg. 1 + Alg. 2) on the whole scene's vector assembled
 from the shard's own rows and halo: a shard's rows read only own and halo
-columns, so its rows of that sweep are exactly the unsplit sweep's rows.  The
-sharded solve must therefore reproduce the unsplit oracle solve bit for bit
-(theta, summed per shard and then over shards, to rounding)."""
+columns, so its rows of that sweep are exactly the unsplit sweep's rows.  A
+D-contact across a cut (a split contact) takes its step in the stand-in's
+second half-sweep from its own endpoint's v* and the other endpoint's v*
+received through the loop's exchange.  The sharded solve must therefore
+reproduce the unsplit oracle solve bit for bit (theta, summed per shard and
+then over shards, to rounding)."""
 import math
 import os
 import socket
@@ -28,9 +31,33 @@ def scene():
     return scenes.terrain_lattice(np.float64, dims=(12, 10, 6))
 
 
+def dofs(nodes):
+    return (3 * np.asarray(nodes, dtype=np.int64)[:, None] + np.arange(3)).ravel()
+
+
+def contact_stage(P, w, v_star):
+    """Alg. 2 and eq. (vup) from a given v* (the second half of the oracle's sweep)."""
+    eta = (P.Jc @ v_star).reshape(-1, 3)
+    rhs = eta.copy()
+    rhs[:, 0] += P.phi
+    lam_star = -np.linalg.solve(ov.gamma_blocks(P, w), rhs[:, :, None])[:, :, 0]
+    lam = ov.project_strict(lam_star, P.mu)
+    return v_star + w * (P.Jc.T @ lam.ravel())
+
+
+def row_stats(P, nodes):
+    """[6 per node]: a_rr of the node's three rows, then their ||A_r*||^2."""
+    A = P.A.tocsr()
+    r = dofs(nodes).reshape(-1, 3)
+    d = A.diagonal()[r]
+    q = np.asarray(A.multiply(A).sum(axis=1)).ravel()[r]
+    return np.concatenate([d, q], axis=1).ravel()
+
+
 class OracleShard:
     """Stand-in for a shard's library context: the oracle's sweep on the
-    assembled vector, the shard's rows kept."""
+    assembled vector, the shard's rows kept; split contacts finish in a second
+    half-sweep, as in the library."""
 
     def __init__(self, P, w, plan):
         self.P, self.w, self.plan = P, w, plan
@@ -38,6 +65,12 @@ class OracleShard:
         self.halo_dofs = (3 * plan.halo[:, None] + np.arange(3)).ravel()
         self.h = np.zeros(3 * len(plan.halo))
         self.v = None
+        m = plan.contacts[plan.split]
+        ni, nj = P.node_i[m], P.node_j[m]
+        here = (ni >= plan.n0) & (ni < plan.n1)
+        self.split_own = np.where(here, ni, nj)          # global endpoint nodes
+        self.split_other = np.where(here, nj, ni)
+        self.stats_set = len(m) == 0
 
     def set_velocity(self, v):
         self.v = np.array(v, dtype=np.float64)
@@ -53,14 +86,42 @@ class OracleShard:
         vals = np.asarray(vals.cpu() if hasattr(vals, "cpu") else vals, dtype=np.float64)
         self.h[3 * first:3 * first + len(vals)] = vals
 
-    def shard_sweep(self):
+    def shard_sweep(self, sumsq=True):
         full = np.zeros(self.P.n)
         full[self.own] = self.v
         full[self.halo_dofs] = self.h
-        new = ov.sweep(self.P, self.w, full).v_next[self.own]
+        r = ov.sweep(self.P, self.w, full)
+        new = r.v_next[self.own]
+        loc = dofs(self.split_own) - 3 * self.plan.n0
+        new[loc] = self.v[loc]                   # split endpoints: v^l until the second half
+        self.vstar = r.v_star
         d = new - self.v
         self.v = new
-        return math.fsum(d * d)
+        self.s2 = math.fsum(d * d)
+        return self.s2 if sumsq else None
+
+    def split_stats(self, out):
+        out.copy_(torch.from_numpy(row_stats(self.P, self.split_own)))
+        return out
+
+    def set_split_stats(self, partner):
+        # what arrives for each split contact is its other endpoint's statistics
+        assert np.array_equal(np.asarray(partner), row_stats(self.P, self.split_other))
+        self.stats_set = True
+
+    def split_vstar(self, out):
+        out.copy_(torch.from_numpy(self.vstar[dofs(self.split_own)]))
+        return out
+
+    def finish_split(self, partner):
+        assert self.stats_set
+        vs = self.vstar.copy()
+        vs[dofs(self.split_other)] = np.asarray(partner)
+        new = contact_stage(self.P, self.w, vs)[dofs(self.split_own)]
+        loc = dofs(self.split_own) - 3 * self.plan.n0
+        d = new - self.v[loc]
+        self.v[loc] = new
+        return self.s2 + math.fsum(d * d)
 
 
 def test_partition_covers_every_node_with_balanced_blocks():
@@ -100,14 +161,67 @@ def test_plans_agree_on_what_each_pair_exchanges():
     assert len(plans[0].halo) == 12 * 10
 
 
-def test_contacts_across_shards_are_refused():
-    sc = scenes.random_problem(np.random.default_rng(3), 40, 6, d_contacts=6, density=0.2)
-    ranges = shard.partition(sc.row_ptr, 2)
-    cross = (sc.node_j >= 0) & ((sc.node_i < ranges[0][1]) != (sc.node_j < ranges[0][1]))
-    if not cross.any():
-        pytest.skip("seed gave no contact across the cut")
-    with pytest.raises(ValueError):
-        shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, 0)
+def split_scene(seed=3, n=60, d=14):
+    """Random SPD problem with S- and D-contacts; D-contacts pair random nodes,
+    so about half of them cross any cut."""
+    return scenes.random_problem(np.random.default_rng(seed), n, 8, d_contacts=d, density=0.08,
+                                 couple=0.4)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_split_contact_plans(k):
+    """Every contact is held by the shards of its nodes and reported by the
+    shard of its lower-numbered node; local node indices map back to the
+    scene's; two shards list the split contacts they share in the same order."""
+    sc = split_scene()
+    ranges = shard.partition(sc.row_ptr, k)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(k)]
+    owner = shard.owner_of(ranges, np.arange(sc.n_nodes))
+    n_split = 0
+    for m in range(sc.n_c):
+        i, j = sc.node_i[m], sc.node_j[m]
+        holders = {int(owner[i])} | ({int(owner[j])} if j >= 0 else set())
+        assert {pl.rank for pl in plans if m in pl.contacts} == holders
+        low = i if j < 0 else min(i, j)
+        assert [pl.rank for pl in plans if m in pl.contacts[pl.owns]] == [int(owner[low])]
+        n_split += len(holders) == 2
+    assert n_split >= 3
+    for pl in plans:
+        def glob(q):
+            return np.where(q < pl.n_own, q + pl.n0, pl.halo[np.maximum(q - pl.n_own, 0)])
+        assert np.array_equal(glob(pl.node_i), sc.node_i[pl.contacts])
+        dj = pl.node_j >= 0
+        assert np.array_equal(glob(pl.node_j[dj]), sc.node_j[pl.contacts][dj])
+        assert (pl.node_j[~dj] == -1).all()
+        # the rows' halo first (it alone is exchanged every sweep), then the other
+        # endpoints of split contacts that no row references
+        assert pl.n_halo_rows == len(shard.halo_of(sc.row_ptr, sc.col_idx, pl.n0, pl.n1))
+        assert sum(n for _, n in pl.recv.values()) == pl.n_halo_rows
+        for p, idx in pl.split_peer.items():
+            q = plans[p]
+            mine = pl.contacts[pl.split[idx]]
+            assert np.array_equal(mine, q.contacts[q.split[q.split_peer[pl.rank]]])
+            assert np.all(np.diff(mine) > 0)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_split_contacts_in_one_process_reproduce_the_unsplit_solve(k):
+    sc = split_scene()
+    P = oracle_problem(sc)
+    w = ov.frobenius_w(P)
+    ranges = shard.partition(sc.row_ptr, k)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(k)]
+    assert all(len(pl.split) for pl in plans)
+    for sweeps in (1, 2, 25):
+        ref = ov.solve(P, w, sc.v0, theta_th=0.0, l_max=sweeps)
+        engines = [OracleShard(P, w, pl) for pl in plans]
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
+                              dtype=torch.float64, device="cpu")
+        assert r.iters == sweeps
+        assert np.array_equal(r.v, ref.v), sweeps
+        assert abs(r.theta - ref.theta) <= 1e-13 * ref.theta
 
 
 def _unsplit(sc):
@@ -137,19 +251,20 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out_dir):
+def _rank_main(rank, world, port, out_dir, kind="lattice"):
     import torch.distributed as dist
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
     try:
-        sc = scene()
+        sc = scene() if kind == "lattice" else split_scene()
         P = oracle_problem(sc)
         w = ov.frobenius_w(P)
         ranges = shard.partition(sc.row_ptr, world)
         plan = shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, rank)
         eng = OracleShard(P, w, plan)
+        th, lm, norm = (THETA, L_MAX, "rms") if kind == "lattice" else (0.0, SPLIT_SWEEPS, "abs")
         r = shard.solve(eng, plan, shard.TorchComm(dist, "cpu"), sc.v0[3 * plan.n0:3 * plan.n1],
-                        n_dof=sc.n, theta_th=THETA, l_max=L_MAX, norm="rms",
+                        n_dof=sc.n, theta_th=th, l_max=lm, norm=norm,
                         dtype=torch.float64, device="cpu")
         np.savez(os.path.join(out_dir, f"r{rank}.npz"), v=r.v, iters=r.iters, theta=r.theta,
                  status=r.status)
@@ -168,4 +283,24 @@ def test_gloo_ranks_reproduce_the_unsplit_solve(world, tmp_path):
     assert all(int(g["iters"]) == ref.iters for g in got)
     assert all(float(g["theta"]) == float(got[0]["theta"]) for g in got)   # one decision
     assert abs(float(got[0]["theta"]) - ref.theta) <= 1e-14 * ref.theta
+    assert np.array_equal(np.concatenate([g["v"] for g in got]), ref.v)
+
+
+SPLIT_SWEEPS = 20
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_with_split_contacts_reproduce_the_unsplit_solve(world, tmp_path):
+    """D-contacts across the cuts: the split contacts' v* and row statistics
+    travel point to point between the ranks that share them."""
+    import torch.multiprocessing as mp
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path), "split"),
+                       nprocs=world, start_method="spawn")
+    sc = split_scene()
+    P = oracle_problem(sc)
+    ref = ov.solve(P, ov.frobenius_w(P), sc.v0, theta_th=0.0, l_max=SPLIT_SWEEPS)
+    got = [np.load(tmp_path / f"r{r}.npz") for r in range(world)]
+    assert all(int(g["iters"]) == SPLIT_SWEEPS for g in got)
+    assert all(float(g["theta"]) == float(got[0]["theta"]) for g in got)
+    assert abs(float(got[0]["theta"]) - ref.theta) <= 1e-13 * ref.theta
     assert np.array_equal(np.concatenate([g["v"] for g in got]), ref.v)
