@@ -149,6 +149,36 @@ __device__ __forceinline__ double cheb_nu(int l, int l_s, double rho, double nu_
   return 4.0 / (4.0 - rho * rho * nu_prev);
 }
 
+// Alg. 3's scalars across sweeps, kept in shared memory (entries 35..38 of a
+// kernel's reduction array) and advanced once per sweep by thread 0, the
+// thread that forms theta (FP64 divisions are slow on this part, and no other
+// thread holds registers for them): after sweep l with residual theta_l, rho
+// of eq. (varrho) and the weight nu of sweep l + 1.  reset() before a solve:
+// the first sweep's nu is 1.
+struct ChebScalars {
+  double nu, rho, th1, th2;
+  __device__ __forceinline__ void reset() {
+    nu = 1.0;
+    rho = th1 = th2 = 0.0;
+  }
+  __device__ __forceinline__ double advance(int l, int l_s, double theta) {
+    // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
+    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
+    th2 = th1;
+    th1 = theta;
+    nu = cheb_nu(l + 1, l_s, rho, nu);
+    return nu;
+  }
+};
+
+// A kernel's Chebyshev scalars (in its reduction array red[40]), or null when
+// the solve is plain Alg. 1; reset by thread 0, the only thread that uses them.
+__device__ __forceinline__ ChebScalars* cheb_scalars(double* red, int l_s) {
+  ChebScalars* cs = l_s > 0 ? reinterpret_cast<ChebScalars*>(red + 35) : nullptr;
+  if (cs && threadIdx.x == 0) cs->reset();
+  return cs;
+}
+
 // v** -> v^{l+1}; vp is this row's v^{l-1} (read only when accelerating).
 template <typename T>
 __device__ __forceinline__ Vec4<T> cheb_combine(const ChebStep<T>& c, const Vec4<T>& vss,
@@ -808,6 +838,35 @@ __device__ __forceinline__ double block_allreduce(double x, double* red) {
   return red[32];
 }
 
+// The same sum, and theta = sqrt(sum) * nscale of Alg. 1 formed once (FP64
+// square roots are slow on this part) and handed to every thread with the sum,
+// with the next sweep's Chebyshev weight (1 when cs is null); red needs 40
+// entries.
+template <int NT>
+__device__ __forceinline__ double block_allreduce_theta(double x, double* red, double nscale,
+                                                        ChebScalars* cs, int l, int l_s,
+                                                        double* theta, double* nu) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    double y = lane < NT / 32 ? red[lane] : 0.0;
+    y = warp_sum(y);
+    if (lane == 0) {
+      const double th = sqrt(y) * nscale;
+      red[32] = y;
+      red[33] = th;
+      red[34] = cs ? cs->advance(l, l_s, th) : 1.0;
+    }
+  }
+  __syncthreads();
+  *theta = red[33];
+  *nu = red[34];
+  return red[32];
+}
+
 // All CTAs arrive; returns false if the wait ran out (the caller then stops).
 // Co-residency of all CTAs is guaranteed by the cooperative launch; the spin
 // is bounded anyway so that a fault elsewhere can never hang the GPU.
@@ -839,25 +898,31 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int& nb
   return *s_ok != 0;
 }
 
-// End of a grid-wide sweep: the CTA's FP64 sum of its warps' partials, the
+// End of a grid-wide sweep: the CTA's FP64 sum of its threads' partials, the
 // grid barrier (as grid_barrier) and the fixed-order sum of every CTA's
 // partial -- computed alike by every CTA, so all take the same stop decision
-// -- with two block barriers instead of six: warp 0 sums the warps' partials,
-// lane 0 publishes the CTA's sum and arrives and waits, __syncwarp passes its
-// acquire on to the warp, which sums the CTAs' partials; the other warps wait
-// at the second block barrier.  `part` is this sweep's half of the partials
-// (the other half may still be read by a CTA that is one barrier behind).
+// -- with two block barriers: warp 0 sums the threads' partials, lane 0
+// publishes the CTA's sum and arrives and waits, __syncwarp passes its acquire
+// on to the warp, which sums the CTAs' partials, and lane 0 forms theta and
+// the next Chebyshev weight; the other warps wait at the second block barrier.
+// `part` is this sweep's half of the partials (the other half may still be
+// read by a CTA that is one barrier behind).
 template <int NT>
 __device__ __forceinline__ bool sweep_sum_barrier(double acc, double* part, unsigned int* bar,
                                                   unsigned int& nb, double* red, int* s_ok,
-                                                  double* total) {
+                                                  double nscale, ChebScalars* cs, int l, int l_s,
+                                                  double* total, double* theta, double* nu) {
+  // every thread's partial staged, warp 0 alone adds them (FP64 adds are slow
+  // on this part: NT / 32 + 4 of them in one warp instead of 5 in every warp)
+  __shared__ double stage[NT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  acc = warp_sum(acc);
-  if (lane == 0) red[wid] = acc;
-  __syncthreads();   // every row of this sweep written, every warp's partial in red
+  stage[threadIdx.x] = acc;
+  __syncthreads();   // every row of this sweep written, every thread's partial staged
   nb += gridDim.x;
   if (wid == 0) {
-    double y = lane < NT / 32 ? red[lane] : 0.0;
+    double y = stage[lane];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) y += stage[w * 32 + lane];
     y = warp_sum(y);
     int ok = 0;
     if (lane == 0) {
@@ -874,12 +939,17 @@ __device__ __forceinline__ bool sweep_sum_barrier(double acc, double* part, unsi
     for (int q = lane; q < (int)gridDim.x; q += 32) s2w += part[q];
     s2w = warp_sum(s2w);
     if (lane == 0) {
+      const double th = sqrt(s2w) * nscale;   // theta of Alg. 1, formed once per CTA
       red[32] = s2w;
+      red[33] = th;
+      red[34] = cs ? cs->advance(l, l_s, th) : 1.0;
       *s_ok = ok;
     }
   }
   __syncthreads();
   *total = red[32];
+  *theta = red[33];
+  *nu = red[34];
   return *s_ok != 0;
 }
 
@@ -911,20 +981,21 @@ __device__ __forceinline__ double scene_threshold(const DevProblem<T>& P, const 
 // so all CTAs take the same stop decision without a further exchange.
 template <typename T, int NT, int MINB, bool PF, bool ADJ, bool SYM = false>
 __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
-  __shared__ double red[33];
+  __shared__ double red[40];
   __shared__ int s_ok;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   unsigned int nbar = 0;   // barriers passed x gridDim.x
-  double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
+  double theta = 0.0, s2 = 0.0, nu = 1.0, bb_alpha = ctl.bb_alpha0;
+  const double nscale = ctl.norm_scale[0];
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
-    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
@@ -976,19 +1047,14 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       }
     }
     if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
-                               &s2)) {
+                               nscale, cs, l, ctl.cheb_ls, &s2, &theta, &nu)) {
       st = ST_TIMEOUT;
       break;
     }
-    theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
     if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
-    // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
-    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
-    th2 = th1;
-    th1 = theta;
   }
   if (st != ST_TIMEOUT && cur == 1) {
     // the latest iterate lives in v1: copy the rows this warp owns into v0
@@ -1115,7 +1181,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   constexpr int NW = NT / 32;
   constexpr int VW = G::VW;
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ double red[33];
+  __shared__ double red[40];
   __shared__ int s_ok;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * NW + wib, nw = gridDim.x * NW;
@@ -1130,13 +1196,14 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
   unsigned int nbar = 0;   // barriers passed x gridDim.x
-  double theta = 0.0, s2 = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  double theta = 0.0, s2 = 0.0, nu = 1.0;
+  const double nscale = ctl.norm_scale[0];
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
-    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
@@ -1190,15 +1257,20 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
             a2 = fma(m[6][e], x.x, fma(m[7][e], x.y, fma(m[8][e], x.z, a2)));
           }
         } else {
-          for (int t = 0; t < ntail; ++t) {
-            const int cc = sc[t * 32 + lane];
-            T mm[9];
+          // leftover entries: every gather of v first (they overlap instead of
+          // forming a chain), then the FMAs in entry order from shared memory
+          Vec4<T> xt[VW - 1];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) mm[q] = sv[t * 288 + q * 32 + lane];
-            const Vec4<T> x = ldv(vin + cc);
-            a0 = fma(mm[0], x.x, fma(mm[1], x.y, fma(mm[2], x.z, a0)));
-            a1 = fma(mm[3], x.x, fma(mm[4], x.y, fma(mm[5], x.z, a1)));
-            a2 = fma(mm[6], x.x, fma(mm[7], x.y, fma(mm[8], x.z, a2)));
+          for (int t = 0; t < VW - 1; ++t)
+            if (t < ntail) xt[t] = ldv(vin + sc[t * 32 + lane]);
+#pragma unroll
+          for (int t = 0; t < VW - 1; ++t) {
+            if (t < ntail) {
+              const T* mm = sv + t * 288 + lane;
+              a0 = fma(mm[0], xt[t].x, fma(mm[32], xt[t].y, fma(mm[64], xt[t].z, a0)));
+              a1 = fma(mm[96], xt[t].x, fma(mm[128], xt[t].y, fma(mm[160], xt[t].z, a1)));
+              a2 = fma(mm[192], xt[t].x, fma(mm[224], xt[t].y, fma(mm[256], xt[t].z, a2)));
+            }
           }
         }
         __syncwarp();
@@ -1226,18 +1298,14 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
         acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
     if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
-                               &s2)) {
+                               nscale, cs, l, ctl.cheb_ls, &s2, &theta, &nu)) {
       st = ST_TIMEOUT;
       break;
     }
-    theta = sqrt(s2) * ctl.norm_scale[0];
     cur ^= 1;
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
     if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
-    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
-    th2 = th1;
-    th1 = theta;
   }
   if (st != ST_TIMEOUT && cur == 1) {
     for (int s = gw; s < P.n_slices; s += nw) {
@@ -1258,7 +1326,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
 // queue and run the whole V-FPI loop of a scene with block-level syncs only.
 template <typename T, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl ctl) {
-  __shared__ double red[33];
+  __shared__ double red[40];
   __shared__ int s_q;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -1275,13 +1343,13 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
     double th_adj = 0.0;
     if constexpr (ADJ) th_adj = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
     int cur = 0, l = 1, st = ST_NOT_CONVERGED;
-    double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0, bb_alpha = ctl.bb_alpha0;
+    double theta = 0.0, nu = 1.0, bb_alpha = ctl.bb_alpha0;
+    ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
     for (;; ++l) {
       const Vec4<T>* vin = cur ? P.v1 : P.v0;
       Vec4<T>* vout = cur ? P.v0 : P.v1;
       ChebStep<T> ch;
-      ch.on = ctl.cheb_ls > 0 ? 1 : 0;
-      nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+      ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
       ch.accel = ch.on && l >= ctl.cheb_ls;
       ch.nu = (T)nu;
       ch.u = (T)ctl.cheb_u;
@@ -1311,14 +1379,11 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
             acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
         }
       }
-      theta = sqrt(block_allreduce<NT>(acc, red)) * nscale;
+      block_allreduce_theta<NT>(acc, red, nscale, cs, l, ctl.cheb_ls, &theta, &nu);
       cur ^= 1;
       if (!isfinite(theta)) { st = ST_NONFINITE; break; }
       if (theta < (ADJ ? th_adj : ctl.theta_th)) { st = ST_OK; break; }
       if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
-      if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
-      th2 = th1;
-      th1 = theta;
     }
     if (cur == 1) {
       for (int s = s0 + wid; s < s1; s += NT / 32) {
@@ -1541,13 +1606,13 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
   double th_adj = 0.0;
   if constexpr (ADJ) th_adj = scene_threshold<T, NT>(P, ctl, s0, s1, nscale, red);
   int cur = 0, l = 1, status = ST_NOT_CONVERGED;
-  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  double theta = 0.0, nu = 1.0;
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
-    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
-    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
@@ -1585,22 +1650,26 @@ __device__ __forceinline__ void cluster_scene(const DevProblem<T>& P, const Solv
       for (int d = d0 + g * NT + threadIdx.x; d < d1; d += G * NT)
         acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
-    double part = block_allreduce<NT>(acc, red);
     if (G > 1) {
+      double part = block_allreduce<NT>(acc, red);
       double* sl = slot + (l & 1) * G;
       if (threadIdx.x == 0) sl[g] = part;
       cluster_sync();
       part = 0.0;
       for (int k = 0; k < G; ++k) part += __ldcg(sl + k);
+      theta = sqrt(part) * nscale;
+      if (cs) {   // (thread 0 advances, everyone takes nu)
+        if (threadIdx.x == 0) red[34] = cs->advance(l, ctl.cheb_ls, theta);
+        __syncthreads();
+        nu = red[34];
+      }
+    } else {
+      block_allreduce_theta<NT>(acc, red, nscale, cs, l, ctl.cheb_ls, &theta, &nu);
     }
-    theta = sqrt(part) * nscale;
     cur ^= 1;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
     if (theta < (ADJ ? th_adj : ctl.theta_th)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
-    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
-    th2 = th1;
-    th1 = theta;
   }
   if (cur == 1) {
     for (int s = a + wid; s < b; s += NT / 32) {
@@ -1758,15 +1827,15 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
   if constexpr (ADJ)
     th_adj = scene_threshold<T, NT>(P, ctl, ctl.scene_slice[sc], ctl.scene_slice[sc + 1], nscale, red);
   int l = 1, status = ST_NOT_CONVERGED, fin = 0;
-  double theta = 0.0, nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+  double theta = 0.0, nu = 1.0;
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
   for (;; ++l) {
     const int pb = (l - 1) & 1, nb = pb ^ 1;
     const Vec4<T>* Vp = pb ? V1 : V0;
     Vec4<T>* Vn = pb ? V0 : V1;
     if (G > 1 && threadIdx.x == 0) mbar_arrive_expect_tx(mbar_v + nb, (uint32_t)expect);
     ChebStep<T> ch;
-    ch.on = ctl.cheb_ls > 0 ? 1 : 0;
-    nu = ch.on ? cheb_nu(l, ctl.cheb_ls, rho, nu) : 1.0;
+    ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
     ch.accel = ch.on && l >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
@@ -1790,7 +1859,9 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
         }
       }
     }
-    double part = block_allreduce<NT>(acc, red);
+    double part = G > 1 ? block_allreduce<NT>(acc, red)
+                        : block_allreduce_theta<NT>(acc, red, nscale, cs, l, ctl.cheb_ls,
+                                                    &theta, &nu);
     if (G > 1) {
       if (threadIdx.x == 0) {
         slots[nb * 8 + g] = part;
@@ -1812,15 +1883,17 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
       vphase ^= 1u << nb;
       part = 0.0;
       for (int k = 0; k < G; ++k) part += slots[nb * 8 + k];
+      theta = sqrt(part) * nscale;
+      if (cs) {   // (thread 0 advances, everyone takes nu)
+        if (threadIdx.x == 0) red[34] = cs->advance(l, ctl.cheb_ls, theta);
+        __syncthreads();
+        nu = red[34];
+      }
     }
-    theta = sqrt(part) * nscale;
     fin = nb;
     if (!isfinite(theta)) { status = ST_NONFINITE; break; }
     if (theta < (ADJ ? th_adj : ctl.theta_th)) { status = ST_OK; break; }
     if (l >= ctl.l_max) { status = ST_NOT_CONVERGED; break; }
-    if (l >= 3) rho = th2 > 0.0 ? fmin(th1 / th2, 1.0) : 1.0;
-    th2 = th1;
-    th1 = theta;
   }
   const Vec4<T>* Vf = fin ? V1 : V0;
   for (int i = threadIdx.x; i < nr; i += NT) stv(P.v0 + row0 + i, Vf[row0 + i - cmin]);
@@ -1842,7 +1915,7 @@ __device__ __forceinline__ void cluster_scene_dsm(const DevProblem<T>& P, const 
 template <typename T, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_solve_cluster(DevProblem<T> P, SolveCtl ctl) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ double red[33];
+  __shared__ double red[40];
   __shared__ int tab[8][4];
   __shared__ int fits;
   const int C = (int)cluster_nctarank();
@@ -2019,7 +2092,7 @@ __global__ void __launch_bounds__(NT) k_split_finish(DevProblem<T> P, int n,
                                                       const int32_t* __restrict__ own,
                                                       const T* __restrict__ partner,
                                                       double* __restrict__ sumsq) {
-  __shared__ double red[33];
+  __shared__ double red[40];
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += NT) {
     const int m = cs[k], r = own[k];
@@ -2134,7 +2207,7 @@ static __global__ void k_scene_threshold(const int32_t* __restrict__ scene_slice
                                          const double* __restrict__ slice_sumsq,
                                          const double* __restrict__ norm_scale, double theta_th,
                                          double* __restrict__ th) {
-  __shared__ double red[33];
+  __shared__ double red[40];
   const int q = blockIdx.x;
   double acc = 0.0;
   for (int s = scene_slice[q] + threadIdx.x; s < scene_slice[q + 1]; s += 256) acc += slice_sumsq[s];
