@@ -1,0 +1,111 @@
+"""GPU parity on the degenerate inputs of the method: no contacts (the fixed
+point of eq. pgd1 is then the linear solve A v = b), a one-node scene, node
+counts around the 32-row slice boundary, and a batch that mixes such scenes
+with an ordinary lattice.  Each on both kernel paths, against the FP64 oracle
+at fixed sweep counts (the ladder of test_gpu_parity, same tolerances) and,
+where the answer has a closed form, against it."""
+import numpy as np
+import pytest
+
+from oracle import vfpi as ov
+from paper_2201_09212_gb300 import scenes
+from tests.conftest import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2201_09212_gb300 import vfpi  # noqa: E402
+from tests.test_gpu_parity import F32_LADDER, F64_LADDER, close, ladder, rel  # noqa: E402
+
+PATHS = ({"force_path": 1}, {"force_path": 2})
+
+
+def no_contact_scene(dtype):
+    return scenes.random_problem(np.random.default_rng(41), 40, 0, density=0.1, couple=0.5,
+                                 dtype=dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("path", PATHS)
+def test_no_contacts_ladder_and_linear_solve(dtype, path):
+    sc = no_contact_scene(dtype)
+    assert sc.n_c == 0
+    ladder(sc, ks=(1, 2, 10), **path)
+    P = oracle_problem(sc)
+    x = np.linalg.solve(P.A.toarray(), P.b)
+    th = 1e-13 if dtype == np.float64 else 1e-6
+    with vfpi.Solver.from_scene(sc, theta_th=th, l_max=20000, **path) as s:
+        r = s.solve(sc.v0)
+        assert r.status == vfpi.VFPI_OK
+        assert s.get_lambda().size == 0
+    # FP32: the converged iterate carries the rounding of one sweep's A v - b
+    assert rel(r.v, x) <= (1e-11 if dtype == np.float64 else 5e-6), rel(r.v, x)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("path", PATHS)
+def test_one_node_scene(dtype, path):
+    """One node on a plane: one row in a 32-row slice whose other 31 rows are padding."""
+    sc = scenes.random_problem(np.random.default_rng(101), 1, 1, density=0.1, couple=0.5,
+                               dtype=dtype)
+    assert sc.n_nodes == 1 and sc.n_c == 1
+    ladder(sc, ks=(1, 2, 10, 30), **path)
+    with vfpi.Solver.from_scene(sc, **path) as s:
+        assert s.layout()["n_pad"] == 32 and s.layout()["n_slices"] == 1
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 65])
+@pytest.mark.parametrize("path", PATHS)
+def test_node_counts_around_the_slice_boundary(n, path):
+    """31/32/33/65 nodes: a full slice, a padded one, one row in a second or
+    third slice; S- and D-contacts."""
+    rng = np.random.default_rng(100 + n)
+    sc = scenes.random_problem(rng, n, 5, d_contacts=3, density=0.1, couple=0.5)
+    ladder(sc, ks=(1, 3, 15), **path)
+    with vfpi.Solver.from_scene(sc, **path) as s:
+        assert s.layout()["n_slices"] == -(-n // 32)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_batch_with_degenerate_scenes(dtype):
+    """One launch over a one-node scene, a scene without contacts, a 33-node
+    scene with S- and D-contacts and a small lattice: each scene's iterate
+    after k sweeps equals its own oracle iterate, and the converged solve of
+    each scene its own solve."""
+    parts = [
+        scenes.random_problem(np.random.default_rng(101), 1, 1, density=0.1, couple=0.5),
+        scenes.random_problem(np.random.default_rng(41), 40, 0, density=0.1, couple=0.5),
+        scenes.random_problem(np.random.default_rng(133), 33, 5, d_contacts=3, density=0.1,
+                              couple=0.5),
+        scenes.small_lattice(np.float64),
+    ]
+    sc = scenes.concat_scenes(parts, dtype=dtype)
+    tol = F64_LADDER if dtype == np.float64 else F32_LADDER
+    offs = sc.scene_ptr
+    c_off = np.concatenate([[0], np.cumsum([p.n_c for p in parts])])
+    for k in (1, 4, 15):
+        with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=k, force_path=2) as s:
+            r = s.solve(sc.v0)
+            assert np.all(np.asarray(r.iters) == k)
+            lam = s.get_lambda().reshape(-1, 3)
+        for q, p in enumerate(parts):
+            P = oracle_problem(p)
+            ref = ov.solve(P, ov.frobenius_w(P), np.asarray(p.v0, float), theta_th=0.0, l_max=k)
+            vq = r.v[3 * offs[q]:3 * offs[q + 1]]
+            assert close(vq, ref.v, tol), (k, q, rel(vq, ref.v))
+            if p.n_c:
+                assert close(lam[c_off[q]:c_off[q + 1]], ref.lam, 10 * tol), (k, q)
+    # the batch at the stop test = each scene solved alone (bitwise: same rows,
+    # same per-scene sums)
+    th = 1e-12 if dtype == np.float64 else 1e-6
+    with vfpi.Solver.from_scene(sc, theta_th=th, l_max=5000, force_path=2) as s:
+        rb = s.solve(sc.v0)
+    for q, p in enumerate(parts):
+        with vfpi.Solver.from_scene(p, theta_th=th, l_max=5000, force_path=2,
+                                    dtype="f64" if dtype == np.float64 else "f32") as s:
+            rq = s.solve(np.asarray(p.v0, dtype))
+        assert int(rb.iters[q]) == rq.iters
+        assert np.array_equal(rb.v[3 * offs[q]:3 * offs[q + 1]], rq.v), q

@@ -480,3 +480,18 @@ def test_integrate_is_explicit_position_update(rng):
     x = rng.normal(0, 1, 30)
     v = rng.normal(0, 1, 30)
     assert np.array_equal(ov.integrate(x, v, 1e-3), x + 1e-3 * v)
+
+
+def test_without_contacts_the_fixed_point_is_the_linear_solve():
+    """With no contact the V-FPI fixed point of eq. (pgd1) is v = A^{-1} b
+    (W is positive and diagonal): Alg. 1 must reach the direct solution, for
+    the Frobenius W and for W = alpha I with alpha below 2 / lambda_max(A)."""
+    from paper_2201_09212_gb300 import scenes
+    from tests.conftest import oracle_problem
+    sc = scenes.random_problem(np.random.default_rng(41), 40, 0, density=0.1, couple=0.5)
+    P = oracle_problem(sc)
+    x = np.linalg.solve(P.A.toarray(), P.b)
+    for w in (ov.frobenius_w(P), np.full(P.n, 1.0 / np.linalg.eigvalsh(P.A.toarray()).max())):
+        r = ov.solve(P, w, sc.v0, theta_th=1e-13, l_max=100000)
+        assert r.converged
+        assert np.linalg.norm(r.v - x) <= 1e-11 * np.linalg.norm(x)
