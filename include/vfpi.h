@@ -409,8 +409,8 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
  * of a D-contact may be a halo node (a "split" contact: the other shard holds
  * it too, with the roles of the nodes unchanged); an S-contact on a halo node,
  * or a D-contact between two halo nodes, gives VFPI_ERR_INVALID_ARG.  A shard
- * runs on the grid path (full storage), without Chebyshev, Barzilai-Borwein
- * steps, the adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).
+ * runs on the grid path (full storage), without Barzilai-Borwein steps, the
+ * adjoint or vfpi_matvec (VFPI_ERR_UNSUPPORTED).
  *
  * A sweep of the whole scene is then: every shard calls vfpi_shard_sweep; the
  * callers sum the shards' sumsq (theta^2 of Alg. 1 = the sum; rms: / n of the
@@ -418,6 +418,16 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
  * neighbours need with vfpi_get_nodes and sets the rows it receives with
  * vfpi_set_halo.  The package's shard module drives this over
  * torch.distributed (NCCL between GPUs); nothing here communicates.
+ *
+ * Alg. 3 on a shard (vfpi_set_chebyshev, or opts.chebyshev_ls): a sweep's
+ * weight nu (eq. chebyup) depends on the whole scene's residuals (eq.
+ * varrho), which only the caller sees, so after each sweep that the stop
+ * test does not end every shard is given the scene's theta of that sweep
+ * (vfpi_shard_set_theta); vfpi_set_velocity starts the solve again at sweep
+ * 1.  Between launches a shard keeps v^{l-1} next to v^l, as Alg. 3 reads it.
+ * theta is summed over shards in another order than over one scene's CTAs,
+ * so nu, and with it the iterates, agree with the unsplit solve to rounding
+ * (bit for bit without Chebyshev).
  *
  * Split contacts.  The step of a D-contact (Alg. 2) needs v* (eq. pgd1) of
  * both nodes, so on a shard with split contacts a sweep has a second half:
@@ -436,6 +446,13 @@ vfpi_status vfpi_solve_noalloc(const vfpi_bsr* A, const float* b, const vfpi_con
 
 /* info2[0] = n_halo, info2[1] = n_split (the split contacts). */
 vfpi_status vfpi_get_shard_info(vfpi_t ctx, int32_t* info2);
+/* After a sweep that does not end the solve: theta (>= 0) of Alg. 1 for the
+ * whole scene (sqrt of the shards' summed sumsq, times 1 / sqrt(n) of the
+ * whole scene with the rms norm).  The shard's next sweep is the following
+ * one; with Alg. 3 its weight nu comes from the recurrence of eq. varrho and
+ * eq. chebyup on these thetas.  VFPI_ERR_UNSUPPORTED on a context that is not
+ * a shard, VFPI_ERR_NONFINITE for a negative or non-finite theta. */
+vfpi_status vfpi_shard_set_theta(vfpi_t ctx, double theta);
 
 /* One sweep (eq. pgd1, Alg. 2, eq. vup) of this shard's rows from its current
  * iterate and the halo values last set; the iterate advances (the own

@@ -20,9 +20,11 @@ UNITS = ("vfpi_f32", "vfpi_f64", "vfpi_api", "vfpi_noalloc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: only the explicit fma() calls of the block-row product are fused,
 # so every launch shape and kernel variant evaluates the same IEEE operations in
-# source order (bitwise-identical iterates across shapes)
+# source order (bitwise-identical iterates across shapes); -ffp-contract=off does the
+# same for host code (a shard's Chebyshev weights, formed on the host with the
+# kernels' operations)
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
-         "-Wall", "--expt-relaxed-constexpr"]
+         "-Wall", "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

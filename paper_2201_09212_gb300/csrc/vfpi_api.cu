@@ -587,8 +587,6 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
       return arg_fail(nullptr, VFPI_ERR_INVALID_ARG, "a shard (n_halo > 0) is one scene");
     if (o->force_path == 2)
       return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "a shard runs on the grid path");
-    if (o->chebyshev_ls != 0)
-      return arg_fail(nullptr, VFPI_ERR_UNSUPPORTED, "a shard runs plain sweeps (no Chebyshev)");
   }
 
   vfpi_ctx* c = new (std::nothrow) vfpi_ctx;
@@ -910,6 +908,10 @@ vfpi_status vfpi_set_velocity(vfpi_t c, const void* v) {
   const void* dv;
   VFPI_TRY_CUDA(device_view(c, v, c->esz * 3 * (size_t)c->N, 0, &dv));
   VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dv, c->d_v0)));
+  if (c->n_halo > 0) {   // a shard's solve starts again at sweep 1
+    c->shard_l = 1;
+    c->shard_cheb = HostChebScalars{};
+  }
   return VFPI_OK;
 }
 
@@ -1131,6 +1133,27 @@ vfpi_status vfpi_set_halo(vfpi_t c, int32_t first, int32_t n, const void* vals) 
   const void* dv;
   VFPI_TRY_CUDA(device_view(c, vals, c->esz * 3 * (size_t)n, 0, &dv));
   VFPI_TRY_CUDA(DISPATCH(c, set_halo(c, first, n, dv)));
+  return VFPI_OK;
+}
+
+vfpi_status vfpi_shard_set_theta(vfpi_t c, double theta) {
+  CTX_CHECK(c);
+  if (c->n_halo == 0) return arg_fail(c, VFPI_ERR_UNSUPPORTED, "vfpi_shard_set_theta is for shards");
+  if (!std::isfinite(theta) || theta < 0)
+    return arg_fail(c, VFPI_ERR_NONFINITE, "theta must be finite and >= 0");
+  const int l = c->shard_l, l_s = c->opts.chebyshev_ls;
+  if (l_s > 0) {   // the kernels' recurrence (ChebScalars::advance), same operations
+    HostChebScalars& q = c->shard_cheb;
+    // eq. (varrho) with the current l: rho = min(theta_{l-1} / theta_{l-2}, 1)
+    if (l >= 3) q.rho = q.th2 > 0.0 ? std::fmin(q.th1 / q.th2, 1.0) : 1.0;
+    q.th2 = q.th1;
+    q.th1 = theta;
+    const int ln = l + 1;   // nu of sweep l + 1 (Alg. 3)
+    if (ln < l_s) q.nu = 1.0;
+    else if (ln == l_s) q.nu = 2.0 / (2.0 - q.rho * q.rho);
+    else q.nu = 4.0 / (4.0 - q.rho * q.rho * q.nu);
+  }
+  c->shard_l = l + 1;
   return VFPI_OK;
 }
 
@@ -1370,7 +1393,6 @@ vfpi_status vfpi_set_barzilai_borwein(vfpi_t c, int32_t rule, double alpha0) {
 
 vfpi_status vfpi_set_chebyshev(vfpi_t c, int32_t l_s, double u) {
   CTX_CHECK(c);
-  if (l_s) NOT_ON_SHARD(c, "Chebyshev acceleration");
   if (l_s != 0 && (l_s < 4 || !(u > 0 && u <= 1)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "Chebyshev needs l_s >= 4 and 0 < u <= 1");
   if (l_s && c->bb_rule)

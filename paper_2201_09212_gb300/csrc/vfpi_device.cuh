@@ -121,6 +121,13 @@ struct SolveCtl {
   int32_t theta_rel;             // 1: the adjoint stops at theta < theta_th * ||b|| (same norm)
   const double* th_scene;        // grid path: [1] theta_th * ||b||, computed before the launch
   double* sumsq;                 // grid path: [1] the last sweep's sum ||dv||^2 (before scaling)
+  // grid path, a shard's one-sweep launches: the launch's first sweep is sweep
+  // l0 of the solve with Chebyshev weight nu0 (else 1 and 1), and swap_end
+  // trades the two iterate buffers at the end instead of copying, so that the
+  // next launch finds v^{l-1} where Alg. 3 reads it
+  int32_t l0;
+  double nu0;
+  int32_t swap_end;
 };
 
 
@@ -172,10 +179,14 @@ struct ChebScalars {
 };
 
 // A kernel's Chebyshev scalars (in its reduction array red[40]), or null when
-// the solve is plain Alg. 1; reset by thread 0, the only thread that uses them.
-__device__ __forceinline__ ChebScalars* cheb_scalars(double* red, int l_s) {
+// the solve is plain Alg. 1; reset by thread 0, the only thread that uses them
+// (nu0: the first sweep's weight, 1 unless a shard's launch continues a solve).
+__device__ __forceinline__ ChebScalars* cheb_scalars(double* red, int l_s, double nu0 = 1.0) {
   ChebScalars* cs = l_s > 0 ? reinterpret_cast<ChebScalars*>(red + 35) : nullptr;
-  if (cs && threadIdx.x == 0) cs->reset();
+  if (cs && threadIdx.x == 0) {
+    cs->reset();
+    cs->nu = nu0;
+  }
   return cs;
 }
 
@@ -629,9 +640,6 @@ __device__ __forceinline__ double finish_row_core(const DevProblem<T>& P, int ro
     const int cj = __ldg(P.c_j + cs);
     if (cj >= 0) {  // D-contact: stage v* and finish in phase 2
       stv(P.dstar + 2 * cs + (row == cj ? 1 : 0), vn);
-      // a shard's split D-contact (other node in the halo) finishes after the
-      // launch, from the other shard's v*: carry v^l for its residual
-      if (cj >= P.n_pad || __ldg(P.c_i + cs) >= P.n_pad) stv(out, vo);
       return 0.0;
     }
     const ContactRec<T> c = load_contact(P, cs);
@@ -953,6 +961,32 @@ __device__ __forceinline__ bool sweep_sum_barrier(double acc, double* part, unsi
   return *s_ok != 0;
 }
 
+// End of a grid launch whose last sweep left the latest iterate in v1: each
+// warp's rows into v0, or, for a shard (swap_end), the two buffers trade
+// places -- v0 the latest, v1 the one before, which Alg. 3 reads next launch
+// -- except at the own endpoint of a split D-contact, where v0 still holds
+// v^l and v1 v^{l-1} for the second half of the sweep.
+template <typename T>
+__device__ __forceinline__ void end_of_grid_launch(const DevProblem<T>& P, const SolveCtl& ctl,
+                                                   int gw, int nw, int lane) {
+  for (int s = gw; s < P.n_slices; s += nw) {
+    const int row = s * 32 + lane;
+    const Vec4<T> a = ldv(P.v1 + row);
+    if (!ctl.swap_end) {
+      stv(P.v0 + row, a);
+      continue;
+    }
+    const int cs = __ldg(P.cslot + row);
+    if (cs >= 0) {
+      const int cj = __ldg(P.c_j + cs);
+      if (cj >= 0 && (cj >= P.n_pad || __ldg(P.c_i + cs) >= P.n_pad)) continue;
+    }
+    const Vec4<T> b = ldv(P.v0 + row);
+    stv(P.v0 + row, a);
+    stv(P.v1 + row, b);
+  }
+}
+
 // Stop threshold of a scene's adjoint solve over slices [s0, s1): theta_th, or
 // with the relative test theta_th * ||b|| (b = dL/dv, same norm), the sum of
 // squares taken in one fixed order by every CTA that reads the scene.  (The
@@ -988,15 +1022,16 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
   const int nw = gridDim.x * (NT / 32);
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   unsigned int nbar = 0;   // barriers passed x gridDim.x
-  double theta = 0.0, s2 = 0.0, nu = 1.0, bb_alpha = ctl.bb_alpha0;
+  double theta = 0.0, s2 = 0.0, nu = ctl.nu0, bb_alpha = ctl.bb_alpha0;
   const double nscale = ctl.norm_scale[0];
-  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls, ctl.nu0);
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
     ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
-    ch.accel = ch.on && l >= ctl.cheb_ls;
+    const int lg = ctl.l0 + l - 1;   // the solve's sweep index
+    ch.accel = ch.on && lg >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
     double acc = 0.0;
@@ -1047,7 +1082,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       }
     }
     if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
-                               nscale, cs, l, ctl.cheb_ls, &s2, &theta, &nu)) {
+                               nscale, cs, lg, ctl.cheb_ls, &s2, &theta, &nu)) {
       st = ST_TIMEOUT;
       break;
     }
@@ -1056,13 +1091,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
     if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
   }
-  if (st != ST_TIMEOUT && cur == 1) {
-    // the latest iterate lives in v1: copy the rows this warp owns into v0
-    for (int s = gw; s < P.n_slices; s += nw) {
-      const int row = s * 32 + lane;
-      stv(P.v0 + row, ldv(P.v1 + row));
-    }
-  }
+  if (st != ST_TIMEOUT && cur == 1) end_of_grid_launch(P, ctl, gw, nw, lane);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl.iters[0] = l;
     ctl.theta[0] = theta;
@@ -1196,15 +1225,16 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   int cur = 0, l = 1, st = ST_NOT_CONVERGED;
   bool failed = false;
   unsigned int nbar = 0;   // barriers passed x gridDim.x
-  double theta = 0.0, s2 = 0.0, nu = 1.0;
+  double theta = 0.0, s2 = 0.0, nu = ctl.nu0;
   const double nscale = ctl.norm_scale[0];
-  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls);
+  ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls, ctl.nu0);
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
     ChebStep<T> ch;
     ch.on = cs ? 1 : 0;   // nu: this sweep's weight, handed out at the end of the last one
-    ch.accel = ch.on && l >= ctl.cheb_ls;
+    const int lg = ctl.l0 + l - 1;   // the solve's sweep index
+    ch.accel = ch.on && lg >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
     double acc = 0.0;
@@ -1298,7 +1328,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
         acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
     if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
-                               nscale, cs, l, ctl.cheb_ls, &s2, &theta, &nu)) {
+                               nscale, cs, lg, ctl.cheb_ls, &s2, &theta, &nu)) {
       st = ST_TIMEOUT;
       break;
     }
@@ -1307,12 +1337,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
   }
-  if (st != ST_TIMEOUT && cur == 1) {
-    for (int s = gw; s < P.n_slices; s += nw) {
-      const int row = s * 32 + lane;
-      stv(P.v0 + row, ldv(P.v1 + row));
-    }
-  }
+  if (st != ST_TIMEOUT && cur == 1) end_of_grid_launch(P, ctl, gw, nw, lane);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl.iters[0] = l;
     ctl.theta[0] = theta;
@@ -2083,15 +2108,16 @@ __global__ void k_split_vstar(int n, const int32_t* __restrict__ cs, const int32
 }
 
 // The step of each split contact from partner[3k..] (the other endpoint's
-// v*): the own endpoint's v^{l+1} into v0 (where the sweep left v^l), and
-// sumsq[0] += the FP64 sum of their ||v^{l+1} - v^l||^2, taken in a fixed
-// order by one CTA.
+// v*): the own endpoint's v^{l+1} into v0 (where the sweep left v^l; with
+// Alg. 3 combined with v^{l-1} from v1, as the sweep's own rows are), v^l into
+// v1, and sumsq[0] += the FP64 sum of their ||v^{l+1} - v^l||^2, taken in a
+// fixed order by one CTA.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_split_finish(DevProblem<T> P, int n,
                                                       const int32_t* __restrict__ cs,
                                                       const int32_t* __restrict__ own,
                                                       const T* __restrict__ partner,
-                                                      double* __restrict__ sumsq) {
+                                                      ChebStep<T> ch, double* __restrict__ sumsq) {
   __shared__ double red[40];
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += NT) {
@@ -2104,9 +2130,12 @@ __global__ void __launch_bounds__(NT) k_split_finish(DevProblem<T> P, int n,
     Vec4<T> ni, nj;
     if (at_j) d_contact_step(P, m, sp, so, w, w, ni, nj);
     else d_contact_step(P, m, so, sp, w, w, ni, nj);
-    const Vec4<T> nn = at_j ? nj : ni;
+    // v0 holds v^l and v1 v^{l-1} here (the launch left this row): Alg. 3's
+    // combination, then the buffers' order of every other row
     const Vec4<T> o = ldv(P.v0 + r);
+    const Vec4<T> nn = cheb_combine(ch, at_j ? nj : ni, o, P.v1 + r);
     stv(P.v0 + r, nn);
+    stv(P.v1 + r, o);
     acc += sqdiff(nn, o);
   }
   acc = block_allreduce<NT>(acc, red);

@@ -51,6 +51,12 @@ struct Launch {
 
 }  // namespace vfpi
 
+// Alg. 3's scalars of a shard's solve, which the caller drives one sweep at a
+// time (the host copy of the kernels' per-CTA state).
+struct HostChebScalars {
+  double nu = 1.0, rho = 0.0, th1 = 0.0, th2 = 0.0;
+};
+
 // The opaque context behind vfpi_t.
 struct vfpi_ctx {
   int dtype = VFPI_F32;
@@ -64,6 +70,8 @@ struct vfpi_ctx {
   int n_halo = 0;         // shard of a split scene: halo nodes, stored after the n_pad rows
   int n_split = 0;        // shard: D-contacts with one node in the halo (split contacts)
   int split_ready = 0;    // W_FROBENIUS: the split contacts' partner row statistics are set
+  int shard_l = 1;        // shard: the index of its next sweep in the solve
+  HostChebScalars shard_cheb;   // shard: Alg. 3's rho and the next sweep's weight nu
   int64_t n_entries = 0;  // sum of slice lengths; stored block slots = 32 * n_entries
 
   // host copies of the layout and contact bookkeeping

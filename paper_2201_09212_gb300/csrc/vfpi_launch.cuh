@@ -175,11 +175,16 @@ cudaError_t Launch<T>::split_vstar(vfpi_ctx* c, void* out) {
 
 template <typename T>
 cudaError_t Launch<T>::split_finish(vfpi_ctx* c, const void* partner_vstar) {
-  if (c->n_split > 0)
-    k_split_finish<T, 256><<<1, 256, 0, c->stream>>>(dev_problem<T>(c), c->n_split, c->d_split_cs,
-                                                     c->d_split_own,
-                                                     static_cast<const T*>(partner_vstar),
-                                                     c->d_sumsq);
+  if (c->n_split == 0) return cudaSuccess;
+  ChebStep<T> ch;   // the step of the sweep this completes
+  ch.on = c->opts.chebyshev_ls > 0 ? 1 : 0;
+  ch.accel = ch.on && c->shard_l >= c->opts.chebyshev_ls;
+  ch.nu = (T)c->shard_cheb.nu;
+  ch.u = (T)c->opts.chebyshev_u;
+  k_split_finish<T, 256><<<1, 256, 0, c->stream>>>(dev_problem<T>(c), c->n_split, c->d_split_cs,
+                                                   c->d_split_own,
+                                                   static_cast<const T*>(partner_vstar), ch,
+                                                   c->d_sumsq);
   return cudaGetLastError();
 }
 
@@ -477,6 +482,12 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.theta_rel = (adjoint && c->adj_tol_set && c->adj_rel) ? 1 : 0;
   ctl.th_scene = c->d_thscene;
   ctl.sumsq = c->d_sumsq;
+  // a shard's launch is one sweep of a solve the caller drives: its index and
+  // weight come from the context, and the iterate buffers keep v^{l-1}
+  const bool shard = c->n_halo > 0 && !adjoint;
+  ctl.l0 = shard ? c->shard_l : 1;
+  ctl.nu0 = shard ? c->shard_cheb.nu : 1.0;
+  ctl.swap_end = shard ? 1 : 0;
   if (ctl.theta_rel && c->path == 1 && c->n_slices > 0) {   // (the per-scene kernels compute theirs)
     k_slice_sumsq<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
         c->n_slices, static_cast<const Vec4<T>*>(c->d_adj_g), c->d_slicesq);

@@ -20,8 +20,9 @@ scene is
 
 Before the first sweep the shards of each split contact also exchange the row
 statistics the tied Frobenius W of its two nodes is formed from (Sec. IV.C).
-The solve is plain Alg. 1 (the Chebyshev weights of Alg. 3 are not carried
-across the per-sweep launches).  This module is the host side only: the
+After every sweep that goes on, each shard is given the scene's theta
+(``vfpi_shard_set_theta``): with Alg. 3 (shards made with ``chebyshev_ls``)
+the next sweep's weight comes from it.  This module is the host side only: the
 partition, the halo, send and split lists, the exchange over
 ``torch.distributed`` (NCCL between GPUs, gloo on CPUs) or inside one process,
 and the loop; every step of the sweep runs in the library's kernels.
@@ -271,8 +272,9 @@ def _split_shapes(plan, width):
 
 
 def _theta(s2: float, n_dof: int, norm: str) -> float:
+    """theta of Alg. 1 as the kernels form it (sqrt, times 1 / sqrt(n))."""
     th = math.sqrt(s2)
-    return th / math.sqrt(n_dof) if norm == "rms" else th
+    return th * (1.0 / math.sqrt(n_dof)) if norm == "rms" else th
 
 
 @dataclasses.dataclass
@@ -320,6 +322,7 @@ def solve(engine, plan: ShardPlan, comm: TorchComm, v0_own, *, n_dof: int, theta
             break
         if l == l_max:
             break
+        engine.shard_set_theta(theta)
         _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
                                               recv_shapes, dtype))
     return ShardResult(engine.get_velocity(), l, theta, status)
@@ -378,6 +381,8 @@ def solve_local(engines, plans, v0, *, n_dof: int, theta_th: float, l_max: int,
             break
         if l == l_max:
             break
+        for e in engines:
+            e.shard_set_theta(theta)
         exchange()
     v = np.concatenate([np.asarray(e.get_velocity()) for e in engines])
     return ShardResult(v, l, theta, status)

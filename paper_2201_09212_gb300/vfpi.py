@@ -40,7 +40,7 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_last_error", "vfpi_status_string", "vfpi_destroy", "vfpi_solve_noalloc",
             "vfpi_noalloc_last_error", "vfpi_shard_sweep", "vfpi_get_nodes", "vfpi_set_halo",
             "vfpi_get_shard_info", "vfpi_get_split_stats", "vfpi_set_split_stats",
-            "vfpi_get_split_vstar", "vfpi_finish_split")
+            "vfpi_get_split_vstar", "vfpi_finish_split", "vfpi_shard_set_theta")
 
 
 class VfpiError(RuntimeError):
@@ -128,6 +128,7 @@ def lib():
         "vfpi_set_split_stats": (st, [vp, vp]),
         "vfpi_get_split_vstar": (st, [vp, vp]),
         "vfpi_finish_split": (st, [vp, vp, vp]),
+        "vfpi_shard_set_theta": (st, [vp, C.c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -318,6 +319,12 @@ class Solver:
         s2 = C.c_double()
         self._check(self._L.vfpi_shard_sweep(self._h, C.byref(s2)))
         return float(s2.value)
+
+    def shard_set_theta(self, theta):
+        """The whole scene's theta of the sweep just taken (the solve goes on):
+        the shard's next sweep follows it, with Alg. 3 at the weight these
+        thetas give."""
+        self._check(self._L.vfpi_shard_set_theta(self._h, float(theta)))
 
     def shard_info(self):
         """(n_halo, n_split): halo nodes and split contacts (D-contacts with one

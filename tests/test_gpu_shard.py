@@ -108,12 +108,16 @@ def test_shard_entry_points_check_their_arguments(lattice):
         with pytest.raises(vfpi.VfpiError) as x:
             e.set_halo(len(pl.halo) - 1, np.zeros(6, np.float32))
         assert x.value.status == code["VFPI_ERR_INVALID_ARG"]
-        for call in (lambda: e.solve(sc.v0[:3 * pl.n_own]), lambda: e.set_chebyshev(5),
+        for call in (lambda: e.solve(sc.v0[:3 * pl.n_own]), lambda: e.set_adjoint_chebyshev(5),
                      lambda: e.matvec(np.zeros(3 * pl.n_own, np.float32)),
                      lambda: e.adjoint(np.zeros(3 * pl.n_own, np.float32))):
             with pytest.raises(vfpi.VfpiError) as x:
                 call()
             assert x.value.status == code["VFPI_ERR_UNSUPPORTED"]
+        for th in (-1.0, float("nan")):
+            with pytest.raises(vfpi.VfpiError) as x:
+                e.shard_set_theta(th)
+            assert x.value.status == code["VFPI_ERR_NONFINITE"]
         # the halo values are what the row products read: a halo row moved by
         # hand changes the next sweep of the rows next to it, and only those
         e.set_velocity(sc.v0[:3 * pl.n_own])
@@ -130,7 +134,8 @@ def test_shard_entry_points_check_their_arguments(lattice):
     finally:
         for x in engines:
             x.close()
-    # a shard's pattern: a repeated column, a column past the halo, Chebyshev
+    # a shard's pattern: a repeated column, a column past the halo; a whole
+    # scene takes no shard step
     bad = plans[0].col_idx.copy()
     bad[1] = bad[0]
     with pytest.raises(vfpi.VfpiError):
@@ -143,9 +148,10 @@ def test_shard_entry_points_check_their_arguments(lattice):
         vfpi.Solver(pl.row_ptr, bad, sc.vals[pl.blocks], sc.b[:3 * pl.n_own], pl.node_i,
                     pl.node_j, sc.R[pl.contacts], sc.mu[pl.contacts], sc.phi[pl.contacts],
                     n_halo=len(pl.halo))
-    with pytest.raises(vfpi.VfpiError) as x:
-        shard.shard_solver(sc, pl, chebyshev_ls=5)
-    assert x.value.status == code["VFPI_ERR_UNSUPPORTED"]
+    with vfpi.Solver.from_scene(sc) as whole:
+        with pytest.raises(vfpi.VfpiError) as x:
+            whole.shard_set_theta(1.0)
+        assert x.value.status == code["VFPI_ERR_UNSUPPORTED"]
 
 
 def _free_port():
@@ -328,3 +334,74 @@ def test_split_contact_calls_check_their_arguments():
                         np.array([ni], np.int32), np.array([nj], np.int32), sc.R[:1], sc.mu[:1],
                         sc.phi[:1], dtype="f64", n_halo=len(pl.halo))
         assert x.value.status == code["VFPI_ERR_INVALID_ARG"]
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_chebyshev_shards_with_split_contacts_equal_the_unsplit_solve(lattice, k):
+    """Alg. 3 (l_s = 5, u = 1) on the FP32 lattice with D-contacts across the
+    cuts: each shard gets the scene's theta after every sweep and forms the
+    weight from it.  theta is summed per shard first, so the weights can
+    differ from the unsplit solve's in their last bits (FP64); the iterates
+    agree to FP32 rounding after 1, 7 and 30 sweeps, and at the benchmark's
+    stop test with the oracle's Alg. 3."""
+    ranges = shard.partition(lattice.row_ptr, k, align=DIMS[0] * DIMS[1])
+    sc = with_split_d_contacts(lattice, ranges)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(k)]
+    engines = [shard.shard_solver(sc, pl, chebyshev_ls=5, chebyshev_u=1.0) for pl in plans]
+    try:
+        for sweeps in (1, 7, 30):
+            with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=sweeps, force_path=1,
+                                        chebyshev_ls=5, chebyshev_u=1.0) as s:
+                ref = s.solve(sc.v0)
+            r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
+                                  device="cuda")
+            assert np.linalg.norm(r.v - ref.v) <= 1e-6 * np.linalg.norm(ref.v), sweeps
+            lam = lambdas(engines, plans, sc.n_c)
+            ref_lam = np.asarray(ref.lam).reshape(-1, 3)
+            assert np.linalg.norm(lam - ref_lam) <= 1e-5 * np.linalg.norm(ref_lam), sweeps
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=1e-6, l_max=200,
+                              norm="rms", device="cuda")
+        lam = lambdas(engines, plans, sc.n_c)
+    finally:
+        for e in engines:
+            e.close()
+    assert r.status == vfpi.VFPI_OK
+    P = oracle_problem(sc)
+    w = ov.frobenius_w(P)
+    ref = ov.solve_chebyshev(P, w, np.asarray(sc.v0, float), theta_th=1e-6, l_max=200,
+                             l_s=5, u=1.0, norm="rms")
+    assert abs(r.iters - ref.iters) <= 1
+    if r.iters != ref.iters:
+        ref = ov.solve_chebyshev(P, w, np.asarray(sc.v0, float), theta_th=0.0, l_max=r.iters,
+                                 l_s=5, u=1.0)
+    v = np.asarray(r.v, float)
+    assert np.linalg.norm(v - ref.v) <= 1e-5 * np.linalg.norm(ref.v)
+    assert scc_residual(P, v, lam.astype(float)) <= 1e-6
+
+
+def test_chebyshev_shards_in_fp64_against_the_unsplit_solve_and_the_oracle():
+    rng = np.random.default_rng(7)
+    sc = scenes.random_problem(rng, 300, 40, d_contacts=40, density=0.03, couple=0.4)
+    ranges = shard.partition(sc.row_ptr, 2)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(2)]
+    engines = [shard.shard_solver(sc, pl, dtype="f64", chebyshev_ls=5, chebyshev_u=0.9)
+               for pl in plans]
+    try:
+        with vfpi.Solver.from_scene(sc, theta_th=0.0, l_max=12, force_path=1, chebyshev_ls=5,
+                                    chebyshev_u=0.9) as s:
+            ref = s.solve(sc.v0)
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=12,
+                              dtype=torch.float64, device="cuda")
+        assert np.linalg.norm(r.v - ref.v) <= 1e-12 * np.linalg.norm(ref.v)
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=1e-12, l_max=20000,
+                              dtype=torch.float64, device="cuda")
+    finally:
+        for e in engines:
+            e.close()
+    assert r.status == vfpi.VFPI_OK
+    P = oracle_problem(sc)
+    ref = ov.solve_chebyshev(P, ov.frobenius_w(P), sc.v0, theta_th=1e-13, l_max=200000, l_s=5,
+                             u=0.9)
+    assert np.linalg.norm(r.v - ref.v) <= 1e-9 * np.linalg.norm(ref.v)

@@ -57,10 +57,12 @@ def row_stats(P, nodes):
 class OracleShard:
     """Stand-in for a shard's library context: the oracle's sweep on the
     assembled vector, the shard's rows kept; split contacts finish in a second
-    half-sweep, as in the library."""
+    half-sweep, as in the library.  cheb = (l_s, u): Alg. 3's combination on
+    the shard's rows (the oracle's formula), with the weight that the scene's
+    thetas give (shard_set_theta)."""
 
-    def __init__(self, P, w, plan):
-        self.P, self.w, self.plan = P, w, plan
+    def __init__(self, P, w, plan, cheb=None):
+        self.P, self.w, self.plan, self.cheb = P, w, plan, cheb
         self.own = slice(3 * plan.n0, 3 * plan.n1)
         self.halo_dofs = (3 * plan.halo[:, None] + np.arange(3)).ravel()
         self.h = np.zeros(3 * len(plan.halo))
@@ -74,6 +76,23 @@ class OracleShard:
 
     def set_velocity(self, v):
         self.v = np.array(v, dtype=np.float64)
+        self.v_prev = self.v.copy()
+        self.l, self.nu, self.rho, self.th1, self.th2 = 1, 1.0, 0.0, 0.0, 0.0
+
+    def shard_set_theta(self, theta):
+        if self.cheb:
+            l_s = self.cheb[0]
+            if self.l >= 3:
+                self.rho = min(self.th1 / self.th2, 1.0) if self.th2 > 0 else 1.0
+            self.th2, self.th1 = self.th1, theta
+            self.nu = ov.chebyshev_nu(self.l + 1, l_s, self.rho, self.nu)
+        self.l += 1
+
+    def _combine(self, vss, v, v_prev):
+        if not self.cheb:
+            return vss
+        u = self.cheb[1]
+        return self.nu * (u * (vss - v) + v - v_prev) + v_prev
 
     def get_velocity(self):
         return self.v.copy()
@@ -91,11 +110,13 @@ class OracleShard:
         full[self.own] = self.v
         full[self.halo_dofs] = self.h
         r = ov.sweep(self.P, self.w, full)
-        new = r.v_next[self.own]
+        new = self._combine(r.v_next[self.own], self.v, self.v_prev)
         loc = dofs(self.split_own) - 3 * self.plan.n0
         new[loc] = self.v[loc]                   # split endpoints: v^l until the second half
+        self.split_prev = self.v_prev[loc].copy()
         self.vstar = r.v_star
         d = new - self.v
+        self.v_prev = self.v
         self.v = new
         self.s2 = math.fsum(d * d)
         return self.s2 if sumsq else None
@@ -117,8 +138,9 @@ class OracleShard:
         assert self.stats_set
         vs = self.vstar.copy()
         vs[dofs(self.split_other)] = np.asarray(partner)
-        new = contact_stage(self.P, self.w, vs)[dofs(self.split_own)]
         loc = dofs(self.split_own) - 3 * self.plan.n0
+        new = self._combine(contact_stage(self.P, self.w, vs)[dofs(self.split_own)], self.v[loc],
+                            self.split_prev)
         d = new - self.v[loc]
         self.v[loc] = new
         return self.s2 + math.fsum(d * d)
@@ -261,7 +283,7 @@ def _rank_main(rank, world, port, out_dir, kind="lattice"):
         w = ov.frobenius_w(P)
         ranges = shard.partition(sc.row_ptr, world)
         plan = shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, rank)
-        eng = OracleShard(P, w, plan)
+        eng = OracleShard(P, w, plan, cheb=(5, 0.9) if kind == "split-cheb" else None)
         th, lm, norm = (THETA, L_MAX, "rms") if kind == "lattice" else (0.0, SPLIT_SWEEPS, "abs")
         r = shard.solve(eng, plan, shard.TorchComm(dist, "cpu"), sc.v0[3 * plan.n0:3 * plan.n1],
                         n_dof=sc.n, theta_th=th, l_max=lm, norm=norm,
@@ -304,3 +326,47 @@ def test_gloo_ranks_with_split_contacts_reproduce_the_unsplit_solve(world, tmp_p
     assert all(float(g["theta"]) == float(got[0]["theta"]) for g in got)
     assert abs(float(got[0]["theta"]) - ref.theta) <= 1e-13 * ref.theta
     assert np.array_equal(np.concatenate([g["v"] for g in got]), ref.v)
+
+
+@pytest.mark.parametrize("kind,k", [("lattice", 2), ("lattice", 3), ("split", 2), ("split", 3)])
+def test_chebyshev_shards_in_one_process_match_the_oracle(kind, k):
+    """Alg. 3 across shards: each shard is given the scene's theta after every
+    sweep and forms the next weight from it; the split solve equals the
+    oracle's Alg. 3 on the whole scene to rounding (theta is summed per shard
+    first, so the weights can differ in their last bits)."""
+    sc = scene() if kind == "lattice" else split_scene()
+    P = oracle_problem(sc)
+    w = ov.frobenius_w(P)
+    ranges = shard.partition(sc.row_ptr, k)
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(k)]
+    for sweeps in (3, 8, 30):
+        ref = ov.solve_chebyshev(P, w, sc.v0, theta_th=0.0, l_max=sweeps, l_s=5, u=0.9)
+        engines = [OracleShard(P, w, pl, cheb=(5, 0.9)) for pl in plans]
+        r = shard.solve_local(engines, plans, sc.v0, n_dof=sc.n, theta_th=0.0, l_max=sweeps,
+                              dtype=torch.float64, device="cpu")
+        assert r.iters == sweeps
+        assert np.linalg.norm(r.v - ref.v) <= 1e-12 * np.linalg.norm(ref.v), sweeps
+        assert abs(r.theta - ref.theta) <= 1e-10 * ref.theta
+    # mid-solve, Alg. 3's iterate is not the plain one
+    plain = ov.solve(P, w, sc.v0, theta_th=0.0, l_max=8)
+    acc = ov.solve_chebyshev(P, w, sc.v0, theta_th=0.0, l_max=8, l_s=5, u=0.9)
+    assert np.linalg.norm(plain.v - acc.v) > 1e-6 * np.linalg.norm(acc.v)
+
+
+def test_gloo_ranks_with_chebyshev_and_split_contacts_match_the_oracle(tmp_path):
+    """Alg. 3 over two gloo ranks with D-contacts across the cut: the scene's
+    theta (all-gathered, summed in rank order) gives both ranks the same
+    weights; the result is the oracle's Alg. 3 on the whole scene to rounding."""
+    import torch.multiprocessing as mp
+    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path), "split-cheb"),
+                       nprocs=2, start_method="spawn")
+    sc = split_scene()
+    P = oracle_problem(sc)
+    ref = ov.solve_chebyshev(P, ov.frobenius_w(P), sc.v0, theta_th=0.0, l_max=SPLIT_SWEEPS,
+                             l_s=5, u=0.9)
+    got = [np.load(tmp_path / f"r{r}.npz") for r in range(2)]
+    assert all(int(g["iters"]) == SPLIT_SWEEPS for g in got)
+    assert float(got[0]["theta"]) == float(got[1]["theta"])
+    v = np.concatenate([g["v"] for g in got])
+    assert np.linalg.norm(v - ref.v) <= 1e-12 * np.linalg.norm(ref.v)
