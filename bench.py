@@ -463,6 +463,41 @@ def sharded_bench(args, torch, dist, dev, sc, dims, rank, ws):
             "note": "one launch and one host round trip per sweep (exchange, residual sum)"}
 
 
+def sharded_one_gpu_bench(args, torch, dev, sc, dims, kernel_ms_per_sweep):
+    """The host-driven loop of the split scene on one GPU: two z-slab shards
+    in one process (shard.solve_local), Alg. 1 to the same stop test.  The
+    shards' launches run one after the other, so the step time above the
+    unsplit kernel's is the loop's own cost per sweep: two launches, the host
+    round trip for the residual sum and the halo rows' exchange."""
+    from paper_2201_09212_gb300 import shard
+    ranges = shard.partition(sc.row_ptr, 2, align=dims[0] * dims[1])
+    plans = [shard.make_plan(sc.row_ptr, sc.col_idx, sc.node_i, sc.node_j, ranges, r)
+             for r in range(2)]
+    engines = [shard.shard_solver(sc, pl) for pl in plans]
+    v0 = torch.from_numpy(np.ascontiguousarray(sc.v0)).to(dev)
+    kw = dict(n_dof=sc.n, theta_th=THETA_TH, l_max=L_MAX, norm="rms", device=dev)
+    try:
+        for _ in range(args.warmup):
+            shard.solve_local(engines, plans, v0, **kw)
+        iters = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.sharded_steps):
+            iters.append(shard.solve_local(engines, plans, v0, **kw).iters)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    finally:
+        for e in engines:
+            e.close()
+    sweeps = float(np.sum(iters))
+    return {"workload": f"{WORKLOAD} in 2 z-slabs, both on this GPU", "ranges": ranges,
+            "halo_nodes": [int(len(pl.halo)) for pl in plans], "steps": args.sharded_steps,
+            "iters_per_step": float(np.mean(iters)), "ms_per_step": 1e3 * t / args.sharded_steps,
+            "dof_iters_per_s": sc.n * sweeps / t,
+            "loop_us_per_sweep_over_unsplit_kernel": 1e6 * t / sweeps - 1e3 * kernel_ms_per_sweep,
+            "note": "the shards' launches one after the other; no device exchange"}
+
+
 def configs_bench(args, torch, dev, stream):
     """The other plain-V-FPI configurations, each solved from its initial
     state repeatedly (tuned launch shape; a 256 MB write between steps flushes
@@ -714,9 +749,12 @@ def main():
     h2d = 4 * (sc.n + sc.n_c + sc.n) + 8 * sc.n
     d2h = 4 * (sc.n + 3 * sc.n_c) + 8 * sc.n
 
-    sharded = None
+    sharded = sharded_one = None
     if ws > 1 and not args.no_sharded:
         sharded = sharded_bench(args, torch, dist, dev, sc, dims, rank, ws)
+    elif not args.no_sharded:
+        sharded_one = sharded_one_gpu_bench(args, torch, dev, sc, dims,
+                                            float(np.mean(kms)) / float(np.mean(iters)))
 
     batched = None
     if not args.no_batched:
@@ -788,6 +826,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "sharded": sharded,
+        "sharded_one_gpu": sharded_one,
         "batched": batched,
         "adjoint": adjoint,
         "configs": configs,

@@ -463,7 +463,9 @@ vfpi_status vfpi_shard_set_theta(vfpi_t ctx, double theta);
 vfpi_status vfpi_shard_sweep(vfpi_t ctx, double* sumsq_out);
 /* Copy the current v of own nodes nodes[0..n) (indices < n_nodes, host or
  * device array) into out [3n] (host or device).  An index out of range gives
- * VFPI_ERR_INVALID_ARG (checked on the device; out is then not written). */
+ * VFPI_ERR_INVALID_ARG and out is not written (a host list is checked on the
+ * host and the call does not wait for the GPU when out is device memory; a
+ * device list is checked on the device, and the call synchronises). */
 vfpi_status vfpi_get_nodes(vfpi_t ctx, const int32_t* nodes, int32_t n, void* out);
 /* Set the v of halo nodes [first, first + n) from vals [3n] (host or device);
  * 0 <= first, first + n <= n_halo. */
@@ -488,8 +490,10 @@ vfpi_status vfpi_get_split_vstar(vfpi_t ctx, void* out);
  * endpoint's v^{l+1} (eq. vup).  sumsq_out (host double, nullable): this
  * shard's whole FP64 ||v^{l+1} - v^l||^2 of the sweep (vfpi_shard_sweep's sum,
  * which leaves out the own endpoints of split contacts, plus theirs);
- * synchronises the stream when set.  With no split contacts it only reads the
- * sum. */
+ * synchronises the stream when set and then reports the sweep's outcome as
+ * vfpi_shard_sweep does (VFPI_ERR_TIMEOUT, ...).  With no split contacts it
+ * only reads the sum, so that a caller can launch several shards' sweeps
+ * (vfpi_shard_sweep with sumsq_out NULL) before waiting for any. */
 vfpi_status vfpi_finish_split(vfpi_t ctx, const void* partner_vstar, double* sumsq_out);
 
 /* Message for the last failing vfpi_solve_noalloc call of this host thread. */

@@ -1108,6 +1108,13 @@ vfpi_status vfpi_get_nodes(vfpi_t c, const int32_t* nodes, int32_t n, void* out)
   if (n < 0 || (n > 0 && (!nodes || !out)))
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "nodes and out are required (n >= 0)");
   if (n == 0) return VFPI_OK;
+  // a host list is checked here, so that the gather needs no wait for the
+  // device's verdict (the sharded loop calls this every sweep)
+  const bool host_nodes = !on_device(nodes);
+  if (host_nodes)
+    for (int32_t k = 0; k < n; ++k)
+      if (nodes[k] < 0 || nodes[k] >= c->N)
+        return arg_fail(c, VFPI_ERR_INVALID_ARG, "vfpi_get_nodes: node index out of range");
   const size_t bytes = c->esz * 3 * (size_t)n;
   const size_t slot = round_up(4 * (size_t)n, 256);
   VFPI_TRY_CUDA(ensure_stage(c, slot + bytes));
@@ -1115,12 +1122,14 @@ vfpi_status vfpi_get_nodes(vfpi_t c, const int32_t* nodes, int32_t n, void* out)
   void* dst;
   VFPI_TRY_CUDA(device_view(c, nodes, 4 * (size_t)n, 0, &dn));
   VFPI_TRY_CUDA(out_view(c, out, bytes, slot, &dst));
-  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  if (!host_nodes) VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   VFPI_TRY_CUDA(DISPATCH(c, gather_nodes(c, static_cast<const int32_t*>(dn), n, dst)));
-  int flags = 0;
-  vfpi_status st = read_err(c, &flags);
-  if (st != VFPI_OK) return st;
-  if (flags) return arg_fail(c, VFPI_ERR_INVALID_ARG, "vfpi_get_nodes: node index out of range");
+  if (!host_nodes) {
+    int flags = 0;
+    vfpi_status st = read_err(c, &flags);
+    if (st != VFPI_OK) return st;
+    if (flags) return arg_fail(c, VFPI_ERR_INVALID_ARG, "vfpi_get_nodes: node index out of range");
+  }
   if (dst != out) VFPI_TRY_CUDA(to_caller(c, out, dst, bytes));
   return VFPI_OK;
 }
@@ -1217,9 +1226,11 @@ vfpi_status vfpi_finish_split(vfpi_t c, const void* partner_vstar, double* sumsq
     VFPI_TRY_CUDA(DISPATCH(c, split_finish(c, dp)));
   }
   if (!sumsq_out) return VFPI_OK;
-  VFPI_TRY_CUDA(cudaMemcpyAsync(sumsq_out, c->d_sumsq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  VFPI_TRY_CUDA(cudaStreamSynchronize(c->stream));
-  return VFPI_OK;
+  double s2 = 0.0;
+  VFPI_TRY_CUDA(cudaMemcpyAsync(&s2, c->d_sumsq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const vfpi_status st = vfpi_get_status(c, nullptr, nullptr);   // synchronises
+  *sumsq_out = s2;
+  return st == VFPI_NOT_CONVERGED ? VFPI_OK : st;
 }
 
 vfpi_status vfpi_solve(vfpi_t c, void* v_inout, void* lambda_out, int32_t* iters_out, double* theta_out) {

@@ -91,6 +91,9 @@ class ShardPlan:
     split: np.ndarray                # positions in ``contacts`` of the split contacts
     split_peer: dict                 # peer -> positions in ``split`` of the contacts shared with it
     owns: np.ndarray                 # [len(contacts)] this shard reports the contact's lambda
+    # the send lists in page-locked host memory (filled on first use with a GPU):
+    # checked on the host and copied by DMA, so that no gather waits for the GPU
+    send_pinned: dict = dataclasses.field(default_factory=dict, repr=False)
 
     @property
     def n_own(self) -> int:
@@ -223,8 +226,8 @@ class LocalComms:
         self.box = {}
 
     def post(self, src: int, sends: dict):
-        for p, t in sends.items():
-            self.box[(src, p)] = t.clone()
+        for p, t in sends.items():     # (fresh tensors: the sender keeps no reference)
+            self.box[(src, p)] = t
 
     def take(self, dst: int, recv_shapes: dict):
         return {p: self.box.pop((p, dst)) for p in recv_shapes}
@@ -236,7 +239,12 @@ class LocalComms:
 
 def _sends(engine, plan, torch, dtype, device):
     out = {}
+    on_gpu = torch.device(device or "cpu").type == "cuda"
     for p, ids in plan.send.items():
+        if on_gpu:
+            if p not in plan.send_pinned:
+                plan.send_pinned[p] = torch.from_numpy(np.ascontiguousarray(ids)).pin_memory()
+            ids = plan.send_pinned[p]
         t = torch.empty(3 * len(ids), dtype=dtype, device=device)
         engine.get_nodes(ids, out=t)
         out[p] = t
@@ -362,14 +370,18 @@ def solve_local(engines, plans, v0, *, n_dof: int, theta_th: float, l_max: int,
     exchange()
     status = NOT_CONVERGED
     theta = float("nan")
+    empty = torch.empty(0, dtype=dtype, device=device)
     for l in range(1, l_max + 1):
-        parts = [e.shard_sweep(sumsq=not len(pl.split)) for e, pl in zip(engines, plans)]
+        # every shard's sweep launched before any sum is waited for
+        for e in engines:
+            e.shard_sweep(sumsq=False)
         if split:
             vs = [e.split_vstar(out=torch.empty(3 * len(pl.split), dtype=dtype, device=device))
                   for e, pl in zip(engines, plans)]
-            for k, (e, x) in enumerate(zip(engines, split_exchange(vs, 3))):
-                if x is not None:
-                    parts[k] = e.finish_split(x)
+            parts = [e.finish_split(x if x is not None else empty)
+                     for e, x in zip(engines, split_exchange(vs, 3))]
+        else:
+            parts = [e.finish_split(empty) for e in engines]
         s2 = 0.0
         for x in parts:
             s2 += x
