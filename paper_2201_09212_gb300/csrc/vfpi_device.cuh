@@ -1204,6 +1204,18 @@ __device__ __forceinline__ bool tma_issue(const DevProblem<T>& P, TmaCursor& cur
   return false;
 }
 
+// The same, run on into the next sweep's stream when this one is all issued
+// (the warp's slices and A are the same every sweep).
+template <typename T>
+__device__ __forceinline__ bool tma_issue_wrap(const DevProblem<T>& P, TmaCursor& cur, int gw,
+                                               int nw, int lane, unsigned char* stage,
+                                               uint64_t* bar) {
+  if (tma_issue(P, cur, nw, lane, stage, bar)) return true;
+  if (gw >= P.n_slices) return false;
+  cur = TmaCursor{gw, 0};
+  return tma_issue(P, cur, nw, lane, stage, bar);
+}
+
 template <typename T, int NT, int NST, bool ADJ>
 __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, SolveCtl ctl) {
   using G = TmaGeom<T>;
@@ -1228,6 +1240,15 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
   double theta = 0.0, s2 = 0.0, nu = ctl.nu0;
   const double nscale = ctl.norm_scale[0];
   ChebScalars* const cs = cheb_scalars(red, ctl.cheb_ls, ctl.nu0);
+  // the warp's chunk stream runs on across sweeps: once a sweep's chunks are
+  // all issued, the ring's free stages take the next sweep's first ones (A
+  // does not change), so each sweep starts with them in flight or landed
+  TmaCursor pc{gw, 0};
+  int issued = 0, consumed = 0;
+  for (int q = 0; q < NST; ++q)
+    if (tma_issue_wrap(P, pc, gw, nw, lane, ring + (size_t)(issued % NST) * G::kStage,
+                       bars + issued % NST))
+      ++issued;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -1238,12 +1259,6 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
     double acc = 0.0;
-    // the warp's chunk stream for this sweep: prefill the ring, then consume
-    TmaCursor pc{gw, 0};
-    int issued = 0, consumed = 0;
-    for (int q = 0; q < NST; ++q)
-      if (tma_issue(P, pc, nw, lane, ring + (size_t)(issued % NST) * G::kStage, bars + issued % NST))
-        ++issued;
     for (int s = gw; s < P.n_slices && !failed; s += nw) {
       const int len = P.slice_len[s];
       const int nfull = len / VW, ntail = len - nfull * VW;
@@ -1305,7 +1320,8 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
         }
         __syncwarp();
         ++consumed;
-        if (tma_issue(P, pc, nw, lane, ring + (size_t)(issued % NST) * G::kStage, bars + issued % NST))
+        if (tma_issue_wrap(P, pc, gw, nw, lane, ring + (size_t)(issued % NST) * G::kStage,
+                           bars + issued % NST))
           ++issued;
       }
       if (failed) break;
@@ -1336,6 +1352,14 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     if (!isfinite(theta)) { st = ST_NONFINITE; break; }
     if (theta < (ADJ && ctl.theta_rel ? ctl.th_scene[0] : ctl.theta_th)) { st = ST_OK; break; }
     if (l >= ctl.l_max) { st = ST_NOT_CONVERGED; break; }
+  }
+  // copies issued for a sweep that will not run: let them land (bounded)
+  // before the CTA exits
+  while (consumed < issued) {
+    const int sg = consumed % NST;
+    mbar_wait(bars + sg, (phase >> sg) & 1u);
+    phase ^= 1u << sg;
+    ++consumed;
   }
   if (st != ST_TIMEOUT && cur == 1) end_of_grid_launch(P, ctl, gw, nw, lane);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
