@@ -28,7 +28,9 @@
  *  - Every array pointer may be host memory (pageable or pinned) or device
  *    memory; the library asks the CUDA runtime which.  Inputs are copied into
  *    library-owned device memory (re-laid out); the caller keeps ownership of
- *    everything it passes and may free it once the call returns.
+ *    everything it passes and may change or free it once the call returns (a
+ *    call given page-locked host input waits for that copy, and with it for
+ *    the work already on the stream).
  *  - Work is enqueued on the stream given to vfpi_create (NULL = legacy default
  *    stream).  Calls that return host scalars, or write to host arrays,
  *    synchronise that stream; the others are asynchronous.

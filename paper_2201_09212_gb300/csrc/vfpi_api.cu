@@ -83,8 +83,15 @@ cudaError_t ensure_stage(vfpi_ctx* c, size_t bytes) {
 // Device view of caller memory: the pointer itself if it is device memory,
 // else a copy at byte offset `slot` of the staging buffer (grown if needed;
 // growing invalidates earlier views, so multi-view callers size it first).
+// The caller may change or free a host array once the call returns: the
+// runtime stages pageable memory before cudaMemcpyAsync returns, but reads
+// page-locked memory when the stream gets there, so that copy is waited for.
 cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot, const void** out) {
-  if (on_device(src)) {
+  cudaPointerAttributes a;
+  int type = cudaMemoryTypeUnregistered;
+  if (src && cudaPointerGetAttributes(&a, src) == cudaSuccess) type = a.type;
+  else cudaGetLastError();
+  if (type == cudaMemoryTypeDevice || type == cudaMemoryTypeManaged) {
     *out = src;
     return cudaSuccess;
   }
@@ -93,7 +100,9 @@ cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot,
   char* dst = static_cast<char*>(c->d_stage) + slot;
   *out = dst;
   if (bytes == 0) return cudaSuccess;
-  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  if ((e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    return e;
+  return type == cudaMemoryTypeHost ? cudaStreamSynchronize(c->stream) : cudaSuccess;
 }
 
 // Write `bytes` of device data to caller memory (host or device).

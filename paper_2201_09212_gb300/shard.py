@@ -91,9 +91,6 @@ class ShardPlan:
     split: np.ndarray                # positions in ``contacts`` of the split contacts
     split_peer: dict                 # peer -> positions in ``split`` of the contacts shared with it
     owns: np.ndarray                 # [len(contacts)] this shard reports the contact's lambda
-    # the send lists in page-locked host memory (filled on first use with a GPU):
-    # checked on the host and copied by DMA, so that no gather waits for the GPU
-    send_pinned: dict = dataclasses.field(default_factory=dict, repr=False)
 
     @property
     def n_own(self) -> int:
@@ -239,12 +236,7 @@ class LocalComms:
 
 def _sends(engine, plan, torch, dtype, device):
     out = {}
-    on_gpu = torch.device(device or "cpu").type == "cuda"
-    for p, ids in plan.send.items():
-        if on_gpu:
-            if p not in plan.send_pinned:
-                plan.send_pinned[p] = torch.from_numpy(np.ascontiguousarray(ids)).pin_memory()
-            ids = plan.send_pinned[p]
+    for p, ids in plan.send.items():   # (host lists: checked on the host, no wait for the GPU)
         t = torch.empty(3 * len(ids), dtype=dtype, device=device)
         engine.get_nodes(ids, out=t)
         out[p] = t

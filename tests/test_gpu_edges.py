@@ -109,3 +109,21 @@ def test_batch_with_degenerate_scenes(dtype):
             rq = s.solve(np.asarray(p.v0, dtype))
         assert int(rb.iters[q]) == rq.iters
         assert np.array_equal(rb.v[3 * offs[q]:3 * offs[q + 1]], rq.v), q
+
+
+def test_page_locked_input_may_change_once_the_call_returns():
+    """A host input may be changed as soon as the call returns, also from
+    page-locked memory (which the runtime reads only when the stream gets to
+    the copy): with a long solve still on the stream, vfpi_set_velocity from a
+    pinned array that is overwritten right after the call keeps the values it
+    was given."""
+    sc = scenes.terrain_lattice(dims=(64, 64, 16))
+    v_new = torch.from_numpy(np.asarray(sc.v0) * 0.5 + 0.25).pin_memory()
+    want = v_new.numpy().copy()
+    with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=200) as s:
+        s.set_velocity(sc.v0)
+        s.solve_async()                      # keeps the stream busy for a while
+        s.set_velocity(v_new)
+        v_new.fill_(float("nan"))            # the caller reuses its buffer
+        got = s.get_velocity()
+    assert np.array_equal(got, want)
