@@ -30,7 +30,8 @@
  *    library-owned device memory (re-laid out); the caller keeps ownership of
  *    everything it passes and may change or free it once the call returns (a
  *    call given page-locked host input waits for that copy, and with it for
- *    the work already on the stream).
+ *    the work already on the stream; under stream capture the copy is a
+ *    graph node instead, which reads the buffer at every replay).
  *  - Work is enqueued on the stream given to vfpi_create (NULL = legacy default
  *    stream).  Calls that return host scalars, or write to host arrays,
  *    synchronise that stream; the others are asynchronous.

@@ -85,7 +85,9 @@ cudaError_t ensure_stage(vfpi_ctx* c, size_t bytes) {
 // growing invalidates earlier views, so multi-view callers size it first).
 // The caller may change or free a host array once the call returns: the
 // runtime stages pageable memory before cudaMemcpyAsync returns, but reads
-// page-locked memory when the stream gets there, so that copy is waited for.
+// page-locked memory when the stream gets there, so that copy is waited for
+// -- unless the stream is being captured, where the copy becomes a graph
+// node that reads the caller's buffer at every replay (the graph's contract).
 cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot, const void** out) {
   cudaPointerAttributes a;
   int type = cudaMemoryTypeUnregistered;
@@ -102,7 +104,10 @@ cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot,
   if (bytes == 0) return cudaSuccess;
   if ((e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
     return e;
-  return type == cudaMemoryTypeHost ? cudaStreamSynchronize(c->stream) : cudaSuccess;
+  if (type != cudaMemoryTypeHost) return cudaSuccess;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(c->stream, &cap)) != cudaSuccess) return e;
+  return cap == cudaStreamCaptureStatusNone ? cudaStreamSynchronize(c->stream) : cudaSuccess;
 }
 
 // Write `bytes` of device data to caller memory (host or device).

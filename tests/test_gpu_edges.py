@@ -127,3 +127,31 @@ def test_page_locked_input_may_change_once_the_call_returns():
         v_new.fill_(float("nan"))            # the caller reuses its buffer
         got = s.get_velocity()
     assert np.array_equal(got, want)
+
+
+def test_page_locked_input_under_stream_capture_is_read_at_each_replay():
+    """Under stream capture the copy from page-locked memory is a graph node:
+    a captured (set_velocity, solve) replays with whatever the pinned buffer
+    holds at replay time, as the eager calls would."""
+    sc = scenes.terrain_lattice(dims=(40, 36, 6))
+    stream = torch.cuda.Stream()
+    v_pin = torch.from_numpy(np.asarray(sc.v0).copy()).pin_memory()
+    starts = [np.asarray(sc.v0) * f for f in (1.0, 0.5, -0.25)]
+    with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=9, force_path=1, stream=stream) as s:
+        ref = []
+        for v in starts:                               # eager
+            s.set_velocity(v)
+            s.solve_async()
+            ref.append(s.get_velocity())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            s.set_velocity(v_pin)                      # warm the path outside capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                s.set_velocity(v_pin)
+                s.solve_async()
+        for v, r in zip(starts, ref):
+            v_pin.copy_(torch.from_numpy(v))
+            g.replay()
+            torch.cuda.synchronize()
+            assert np.array_equal(s.get_velocity(), r)
