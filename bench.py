@@ -49,8 +49,9 @@ ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under
 NCU_TRAFFIC = {("fb6d24c0969c8168", 0): 554678224, ("fb6d24c0969c8168", 7): 553529631}
 # the same for the batched kernel: (DRAM read + write bytes, algorithmic bytes)
 # of one captured env-step solve launch (the bench's launch log gives the
-# captured launch's own count), keyed by source hash
-NCU_BATCH_TRAFFIC = {"fb6d24c0969c8168": (164008244352, 172972435132)}
+# captured launch's own count), keyed by (source hash, "full" or "b6" storage,
+# threads per CTA)
+NCU_BATCH_TRAFFIC = {("fb6d24c0969c8168", "full", 256): (164008244352, 172972435132)}
 
 
 def source_hash() -> str:
@@ -403,8 +404,11 @@ def batched_bench(args, torch, dev, stream, rank):
     lay_b = s.layout()
     threads = lay_b["threads"]
     var = int(tuned.get("kernel_variant", 0))
-    kname = (f"k_solve_cluster<float,{threads}> (launch shape {var})" if var >= 16
-             else f"k_solve_scenes<float,{threads}>")
+    kname = (f"k_solve_cluster<float,{threads}> (launch shape {var})" if 16 <= var <= 25
+             else f"k_solve_scenes<float,{threads}>" + (
+                 " on symmetric blocks (6 values per block streamed; effective fraction)"
+                 if var == 30 else ""))
+    tr_key = (source_hash(), "b6" if var == 30 else "full", threads)
     s.close()
     return {
         "workload": f"{S} lattices, side U{{4..12}}, {int(nq.sum()) * 3} DOF, {sc.nnzb} blocks, {sc.n_c} contacts",
@@ -414,9 +418,8 @@ def batched_bench(args, torch, dev, stream, rank):
         "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
                          "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0],
                          "traffic_over_algorithmic": (
-                             NCU_BATCH_TRAFFIC[source_hash()][0] / NCU_BATCH_TRAFFIC[source_hash()][1]
-                             if source_hash() in NCU_BATCH_TRAFFIC and var < 16 and threads == 256
-                             else None)},
+                             NCU_BATCH_TRAFFIC[tr_key][0] / NCU_BATCH_TRAFFIC[tr_key][1]
+                             if tr_key in NCU_BATCH_TRAFFIC and (var < 16 or var == 30) else None)},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
         "layout": {"blocks": int(sc.nnzb), "stored_slots": int(lay_b["slots"]),
                    "padding": lay_b["slots"] / sc.nnzb - 1.0},
@@ -777,6 +780,7 @@ def main():
         return
 
     sym = 12 <= int(tuned["kernel_variant"]) <= 15
+    b6 = int(tuned["kernel_variant"]) in (28, 29)
     # always the full-BSR count: a compressed storage is reported as an
     # effective fraction next to the measured DRAM bytes, not by a new count
     bps = algorithmic_bytes_per_sweep(sc)
@@ -790,7 +794,9 @@ def main():
                 "traffic": (tr * it_avg if tr else None),
                 "algorithmic_bytes_per_sweep": bps,
                 "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
-                          + (" (symmetric storage; effective fraction)" if sym else ""),
+                          + (" (symmetric storage; effective fraction)" if sym else "")
+                          + (" (symmetric blocks: 6 values per block streamed, the 40-byte"
+                             " full-BSR count kept; effective fraction)" if b6 else ""),
                 "kernel_ms_avg": 1e3 * k_avg}
     cpu = cpu_all = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -816,8 +822,9 @@ def main():
                               "threads": lay["threads"], "tuned_ms_per_sweep": tuned["ms_per_sweep"],
                               "from_cache": tuned["cached"]},
                    "l2": ("inputs larger than L2 (" + (
-                       f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks"
-                       if sym else f"{sc.nnzb * 40 / 1e6:.0f} MB of blocks") + " streamed per sweep)")},
+                       f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks" if sym
+                       else f"{sc.nnzb * 28 / 1e6:.0f} MB of 6-value blocks" if b6
+                       else f"{sc.nnzb * 40 / 1e6:.0f} MB of blocks") + " streamed per sweep)")},
         "roofline": roofline,
         "time_to_solution": time_to_solution,
         "cpu_baseline": cpu,

@@ -119,9 +119,10 @@ typedef struct {
                               scene of at most 64 slices (2,048 nodes), else
                               grid-wide (1); 1 or 2 forces that path; other
                               values: VFPI_ERR_INVALID_ARG                     */
-  int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..15 (threads per
+  int32_t kernel_variant;  /* one of VFPI_VARIANT_*: grid path 0..15, 26..29 (threads per
                               CTA, CTAs/SM register budget, prefetch, TMA ring,
-                              symmetric storage); scene path 0 or
+                              symmetric storage, symmetric blocks); scene path 0,
+                              30 or
                               VFPI_VARIANT_CL_*; with 0 a nonzero block_threads
                               selects that CTA size, unbudgeted                  */
   int32_t grid_ctas;       /* grid path: CTAs of the persistent launch (0 = all that
@@ -192,7 +193,21 @@ enum {
    * twice the warps fit -- for mid-size scenes whose sweeps are bounded by
    * each warp's chain of dependent loads rather than by bandwidth. */
   VFPI_VARIANT_TMA_256_2 = 26,
-  VFPI_VARIANT_TMA_128_2 = 27
+  VFPI_VARIANT_TMA_128_2 = 27,
+  /* Symmetric-block storage, when every 3x3 block of A equals its transpose
+   * bit for bit (checked whenever A is set; a mass-spring lattice's blocks
+   * are): each block streams as its 6 distinct values, 24 + 4 instead of
+   * 36 + 4 bytes, rebuilt to the same 9 entries and FMAs, so the iterates are
+   * bitwise those of the full storage.  Forward solves only (the adjoint and
+   * Barzilai-Borwein steps read the full storage); if a later vfpi_update
+   * makes a block asymmetric, solves fall back to the full storage.  The
+   * 6-value copy (24 bytes per stored slot) is built when the variant is
+   * chosen.  Grid path: VFPI_VARIANT_DEFAULT's and VFPI_VARIANT_256_2's
+   * shapes; scene path: the CTA-per-scene kernel (block_threads picks its
+   * size).  VFPI_ERR_INVALID_ARG for a matrix with an asymmetric block. */
+  VFPI_VARIANT_B6_256_3 = 28,
+  VFPI_VARIANT_B6_256_2 = 29,
+  VFPI_VARIANT_B6_SCENES = 30
 };
 
 /* Fill *o with the defaults: F32, Frobenius W, theta_th 1e-5, l_max 200,

@@ -142,7 +142,8 @@ void free_all(vfpi_ctx* c) {
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
                   c->d_stage, c->d_items, c->d_col_idx, c->d_nlow, c->d_ulen, c->d_llen,
                   c->d_uoff, c->d_loff, c->d_uvals, c->d_ucols, c->d_lcols, c->d_lpos,
-                  c->d_thscene, c->d_slicesq, c->d_sumsq, c->d_split_cs, c->d_split_own};
+                  c->d_thscene, c->d_slicesq, c->d_sumsq, c->d_split_cs, c->d_split_own,
+                  c->d_vals6};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -167,10 +168,12 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
   const bool is_cl = v >= VFPI_VARIANT_CL_256_1_1 && v <= VFPI_VARIANT_CL_128_8_4;
   const bool is_sym = v >= VFPI_VARIANT_SYM_256_2 && v <= VFPI_VARIANT_SYM_512_1;
   const bool is_tma2 = v == VFPI_VARIANT_TMA_256_2 || v == VFPI_VARIANT_TMA_128_2;
-  if (v < 0 || (v > VFPI_VARIANT_SYM_512_1 && !is_cl && !is_tma2)) return false;
+  const bool is_b6 = v >= VFPI_VARIANT_B6_256_3 && v <= VFPI_VARIANT_B6_SCENES;
+  if (v < 0 || (v > VFPI_VARIANT_SYM_512_1 && !is_cl && !is_tma2 && !is_b6)) return false;
   if (c->path == 1 && is_cl) return false;
   if (c->path != 1 && is_tma2) return false;
   if (is_sym && (c->path != 1 || !c->sym_ok)) return false;
+  if (is_b6 && (!c->bsym_ok || (c->path == 1) != (v != VFPI_VARIANT_B6_SCENES))) return false;
   c->nt = block_threads ? block_threads : (c->path == 1 ? 256 : 128);
   c->minb = 1;
   c->pf = 0;
@@ -178,7 +181,11 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
   c->cluster = 0;
   c->cl_per_sm = 1;
   c->sym = 0;
-  if (is_sym) {
+  c->b6 = is_b6 ? 1 : 0;
+  if (is_b6) {
+    if (v == VFPI_VARIANT_B6_256_3) { c->nt = 256; c->minb = 3; }
+    if (v == VFPI_VARIANT_B6_256_2) { c->nt = 256; c->minb = 2; }
+  } else if (is_sym) {
     c->nt = sym_table[v - VFPI_VARIANT_SYM_256_2][0];
     c->minb = sym_table[v - VFPI_VARIANT_SYM_256_2][1];
     c->sym = 1;
@@ -200,15 +207,17 @@ bool apply_variant(vfpi_ctx* c, int v, int block_threads) {
 }
 
 struct Shape {
-  int nt, minb, pf, tma_stages, cluster, cl_per_sm, grid_ctas, sym;
+  int nt, minb, pf, tma_stages, cluster, cl_per_sm, grid_ctas, sym, b6;
 };
 Shape shape_of(const vfpi_ctx* c) {
-  return {c->nt, c->minb, c->pf, c->tma_stages, c->cluster, c->cl_per_sm, c->opts.grid_ctas, c->sym};
+  return {c->nt, c->minb, c->pf, c->tma_stages, c->cluster, c->cl_per_sm, c->opts.grid_ctas, c->sym,
+          c->b6};
 }
 void restore_shape(vfpi_ctx* c, const Shape& s) {
   c->nt = s.nt; c->minb = s.minb; c->pf = s.pf; c->tma_stages = s.tma_stages;
   c->cluster = s.cluster; c->cl_per_sm = s.cl_per_sm; c->opts.grid_ctas = s.grid_ctas;
   c->sym = s.sym;
+  c->b6 = s.b6;
 }
 
 
@@ -496,6 +505,8 @@ vfpi_status set_sym(vfpi_ctx* c, const int32_t* dcol, const void* dv, bool first
 // A's values: checked finite, then scattered into the sliced-ELL layout.  With
 // store_cols the pattern (drow, dcol: device copies) is laid out too; without
 // it only the values are replaced and the stored pattern is reused.
+vfpi_status set_bsym(vfpi_ctx* c);
+
 vfpi_status set_values(vfpi_ctx* c, const int32_t* drow, const int32_t* dcol, const void* vals,
                        bool store_cols, size_t slot) {
   const size_t vbytes = c->esz * 9 * (size_t)c->nnzb;
@@ -508,8 +519,32 @@ vfpi_status set_values(vfpi_ctx* c, const int32_t* drow, const int32_t* dcol, co
   if (st != VFPI_OK) return st;
   if (flags) return arg_fail(c, VFPI_ERR_NONFINITE, "A has non-finite values");
   VFPI_TRY_CUDA(DISPATCH(c, build_layout(c, drow, dcol, dv, store_cols)));
+  if ((st = set_bsym(c)) != VFPI_OK) return st;
   // (a shard keeps the full storage: its rows see halo columns outside A's square)
   if (c->path == 1 && c->n_halo == 0) return set_sym(c, dcol, dv, store_cols);
+  return VFPI_OK;
+}
+
+// Symmetric-block storage: whether every stored block equals its transpose
+// (checked whenever A is set); vals6 is built when a variant that reads it is
+// chosen, and rebuilt with each new A once it exists.
+vfpi_status set_bsym(vfpi_ctx* c) {
+  c->bsym_ok = 0;
+  VFPI_TRY_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  VFPI_TRY_CUDA(DISPATCH(c, block_sym_check(c)));
+  int flags = 0;
+  vfpi_status st = read_err(c, &flags);
+  if (st != VFPI_OK) return st;
+  if (flags & 128) return VFPI_OK;
+  c->bsym_ok = 1;
+  if (c->d_vals6) VFPI_TRY_CUDA(DISPATCH(c, make_vals6(c)));
+  return VFPI_OK;
+}
+
+vfpi_status ensure_vals6(vfpi_ctx* c) {
+  if (!c->b6 || !c->bsym_ok || c->d_vals6) return VFPI_OK;
+  VFPI_TRY_CUDA(dalloc(&c->d_vals6, c->esz * 192 * (size_t)std::max<int64_t>(c->n_entries, 1)));
+  VFPI_TRY_CUDA(DISPATCH(c, make_vals6(c)));
   return VFPI_OK;
 }
 
@@ -846,6 +881,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
     c->err = "unknown kernel_variant for this path";
     return fail(VFPI_ERR_INVALID_ARG);
   }
+  CREATE_ST(ensure_vals6(c));
   if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
   CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
@@ -1298,6 +1334,11 @@ vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t bloc
   if (!apply_variant(c, kernel_variant, block_threads)) {
     restore_shape(c, saved);
     return arg_fail(c, VFPI_ERR_INVALID_ARG, "unknown kernel_variant for this path");
+  }
+  vfpi_status vst = ensure_vals6(c);
+  if (vst != VFPI_OK) {
+    restore_shape(c, saved);
+    return vst;
   }
   c->opts.grid_ctas = grid_ctas;
   const int old_max = c->max_grid;

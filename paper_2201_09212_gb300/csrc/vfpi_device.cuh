@@ -50,6 +50,7 @@ struct DevProblem {
   const int32_t* slice_len;      // [n_slices] entries per lane
   const int64_t* slice_off;      // [n_slices] offset in entries (1 entry = 32 slots)
   const T* vals;                 // sliced-ELL values
+  const T* vals6;                // the same slots, 6 values each, when every block is symmetric
   const int32_t* cols;           // sliced-ELL internal column indices
   const int32_t* slice_cmin;     // [n_slices] smallest / largest column of a slice
   const int32_t* slice_cmax;     //   (padding slots included)
@@ -316,6 +317,66 @@ __device__ __forceinline__ void row_product(const DevProblem<T>& P, int slice, i
     T m[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) m[q] = __ldcs(pt + t * 288 + q * 32);
+    const Vec4<T> x = ldv(vin + c);
+    a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
+    a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
+    a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
+  }
+}
+
+// Symmetric-block storage: when every stored 3x3 block equals its transpose
+// bit for bit (a mass-spring lattice's blocks are multiples of e e^T plus
+// diagonal mass), vals6 keeps each slot's (m00, m01, m02, m11, m12, m22) in
+// the layout of vals with 6 planes instead of 9 (192 values per slot group
+// of 32 rows).  The product rebuilds the 9 entries and runs the same FMAs in
+// the same order, so the iterates are bitwise those of the full storage,
+// from 24 + 4 instead of 36 + 4 bytes per block.
+template <typename T>
+__device__ __forceinline__ void expand6(const T (&q)[6], T (&m)[9]) {
+  m[0] = q[0]; m[1] = q[1]; m[2] = q[2];
+  m[3] = q[1]; m[4] = q[3]; m[5] = q[4];
+  m[6] = q[2]; m[7] = q[4]; m[8] = q[5];
+}
+
+template <typename T>
+__device__ __forceinline__ void row_product6(const DevProblem<T>& P, int slice, int lane,
+                                             const Vec4<T>* vin, T& a0, T& a1, T& a2) {
+  constexpr int VW = Chunk<T>::VW;
+  const int len = P.slice_len[slice];
+  const int64_t off = P.slice_off[slice];
+  const T* __restrict__ vb = P.vals6 + off * 192;
+  const int32_t* __restrict__ cb = P.cols + off * 32;
+  a0 = T(0); a1 = T(0); a2 = T(0);
+  const int nfull = len / VW;
+#pragma unroll 1
+  for (int k = 0; k < nfull; ++k) {
+    int c[VW];
+    T q[6][VW];
+    Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
+    const T* p = vb + (int64_t)k * (192 * VW) + lane * VW;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) Chunk<T>::vals(p + j * (32 * VW), q[j]);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const Vec4<T> x = ldv(vin + c[e]);
+      T qe[6], m[9];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) qe[j] = q[j][e];
+      expand6(qe, m);
+      a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
+      a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
+      a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
+    }
+  }
+  const int ntail = len - nfull * VW;
+  const T* pt = vb + (int64_t)nfull * (192 * VW) + lane;
+  const int32_t* ct = cb + (int64_t)nfull * (32 * VW) + lane;
+  for (int t = 0; t < ntail; ++t) {
+    const int c = __ldcs(ct + t * 32);
+    T qe[6], m[9];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) qe[j] = __ldcs(pt + t * 192 + j * 32);
+    expand6(qe, m);
     const Vec4<T> x = ldv(vin + c);
     a0 = fma(m[0], x.x, fma(m[1], x.y, fma(m[2], x.z, a0)));
     a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
@@ -681,12 +742,13 @@ __device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T 
                                  ldv(P.w + row), __ldg(P.cslot + row), vout + row, ch);
 }
 
-template <typename T, bool ADJ, bool PF = false, bool SYM = false>
+template <typename T, bool ADJ, bool PF = false, bool SYM = false, bool B6 = false>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
                                             const Vec4<T>* vin, Vec4<T>* vout,
                                             const ChebStep<T>& ch) {
   T a0, a1, a2;
-  if constexpr (SYM) row_product_sym(P, slice, lane, vin, a0, a1, a2);
+  if constexpr (B6) row_product6(P, slice, lane, vin, a0, a1, a2);
+  else if constexpr (SYM) row_product_sym(P, slice, lane, vin, a0, a1, a2);
   else if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
   else row_product(P, slice, lane, vin, a0, a1, a2);
   return finish_row<T, ADJ>(P, slice * 32 + lane, a0, a1, a2, vin, vout, ch);
@@ -1013,7 +1075,7 @@ __device__ __forceinline__ double scene_threshold(const DevProblem<T>& P, const 
 // gw, gw + W, ...; one barrier per sweep (two with D-contacts).  theta is the
 // fixed-order sum of the per-CTA partials, computed identically by every CTA,
 // so all CTAs take the same stop decision without a further exchange.
-template <typename T, int NT, int MINB, bool PF, bool ADJ, bool SYM = false>
+template <typename T, int NT, int MINB, bool PF, bool ADJ, bool SYM = false, bool B6 = false>
 __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[40];
   __shared__ int s_ok;
@@ -1074,7 +1136,8 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
           acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
       }
     } else {
-      for (int s = gw; s < P.n_slices; s += nw) acc += sweep_row<T, ADJ, PF, SYM>(P, s, lane, vin, vout, ch);
+      for (int s = gw; s < P.n_slices; s += nw)
+        acc += sweep_row<T, ADJ, PF, SYM, B6>(P, s, lane, vin, vout, ch);
       if (ctl.n_d > 0) {
         if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
@@ -1373,7 +1436,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
 
 // Persistent CTA-per-scene solve: CTAs pop scenes (largest first) from a
 // queue and run the whole V-FPI loop of a scene with block-level syncs only.
-template <typename T, int NT, bool ADJ>
+template <typename T, int NT, bool ADJ, bool B6 = false>
 __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl ctl) {
   __shared__ double red[40];
   __shared__ int s_q;
@@ -1421,7 +1484,8 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
             acc += bb_d_contact(P, P.d_list[d], vin, vout, (T)bb_alpha);
         }
       } else {
-        for (int s = s0 + wid; s < s1; s += NT / 32) acc += sweep_row<T, ADJ>(P, s, lane, vin, vout, ch);
+        for (int s = s0 + wid; s < s1; s += NT / 32)
+          acc += sweep_row<T, ADJ, false, false, B6>(P, s, lane, vin, vout, ch);
         if (d1 > d0) {
           __syncthreads();
           for (int d = d0 + threadIdx.x; d < d1; d += NT)
@@ -2408,6 +2472,53 @@ __global__ void k_row_stats(DevProblem<T> P, double* __restrict__ ds) {
   for (int a = 0; a < 3; ++a) {
     ds[6 * (int64_t)row + a] = d[a];
     ds[6 * (int64_t)row + 3 + a] = q2[a];
+  }
+}
+
+// Symmetric-block storage: err bit 128 unless every stored slot's block equals
+// its transpose bit for bit (one thread per slot: slice s = t / 32 rows,
+// entry e over the slice's length).
+template <typename T>
+__global__ void k_block_sym_check(DevProblem<T> P, int* err) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= P.n_pad) return;
+  const int s = row >> 5, lane = row & 31;
+  const int len = P.slice_len[s];
+  const int64_t off = P.slice_off[s];
+  for (int e = 0; e < len; ++e) {
+    int64_t vp;
+    int vs;
+    slot_pos<T>(off, len, e, lane, &vp, &vs);
+    const T* m = P.vals + vp;
+    if (m[1 * vs] != m[3 * vs] || m[2 * vs] != m[6 * vs] || m[5 * vs] != m[7 * vs]) {
+      atomicOr(err, 128);
+      return;
+    }
+  }
+}
+
+// vals -> vals6 (m00, m01, m02, m11, m12, m22 per slot, the layout of vals
+// with 6 planes: slot_pos with 192 in place of 288).
+template <typename T>
+__global__ void k_make_vals6(DevProblem<T> P, T* __restrict__ vals6) {
+  constexpr int VW = Chunk<T>::VW;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= P.n_pad) return;
+  const int s = row >> 5, lane = row & 31;
+  const int len = P.slice_len[s];
+  const int64_t off = P.slice_off[s];
+  const int nfull = len / VW;
+  for (int e = 0; e < len; ++e) {
+    int64_t vp;
+    int vs;
+    slot_pos<T>(off, len, e, lane, &vp, &vs);
+    int64_t qp;
+    if (e < nfull * VW) qp = off * 192 + (int64_t)(e / VW) * (192 * VW) + lane * VW + e % VW;
+    else qp = off * 192 + (int64_t)nfull * (192 * VW) + (int64_t)(e - nfull * VW) * 192 + lane;
+    const T* m = P.vals + vp;
+    const int src[6] = {0, 1, 2, 4, 5, 8};
+#pragma unroll
+    for (int j = 0; j < 6; ++j) vals6[qp + (int64_t)j * vs] = m[(int64_t)src[j] * vs];
   }
 }
 

@@ -32,6 +32,9 @@ struct Launch {
   static cudaError_t build_layout(vfpi_ctx* c, const int32_t* row_ptr, const int32_t* col_idx,
                                   const void* vals, bool store_cols);
   static cudaError_t make_w(vfpi_ctx* c);
+  // symmetric-block storage: check (err bit 128 if a block is not symmetric), build
+  static cudaError_t block_sym_check(vfpi_ctx* c);
+  static cudaError_t make_vals6(vfpi_ctx* c);
   static cudaError_t row_stats(vfpi_ctx* c);
   static cudaError_t to_internal(vfpi_ctx* c, const void* ext, void* internal);
   static cudaError_t to_external(vfpi_ctx* c, const void* internal, void* ext);
@@ -93,6 +96,9 @@ struct vfpi_ctx {
   void* d_uvals = nullptr;
   int32_t *d_ucols = nullptr, *d_lcols = nullptr, *d_lpos = nullptr;
   void* d_vals = nullptr;
+  void* d_vals6 = nullptr;   // 6 values per slot (built for the symmetric-block variants)
+  int bsym_ok = 0;           // every stored block equals its transpose bit for bit
+  int b6 = 0;                // launch variant reads vals6 (when bsym_ok and built)
   int32_t* d_cols = nullptr;
   void *d_b = nullptr, *d_w = nullptr, *d_v0 = nullptr, *d_v1 = nullptr;
   void *d_t0 = nullptr, *d_t1 = nullptr;    // internal temporaries (matvec)

@@ -19,6 +19,7 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.slice_off = c->d_slice_off;
   P.vals = static_cast<const T*>(c->d_vals);
   P.cols = c->d_cols;
+  P.vals6 = static_cast<const T*>(c->d_vals6);
   P.slice_cmin = c->d_slice_cmin;
   P.slice_cmax = c->d_slice_cmax;
   P.uvals = static_cast<const T*>(c->d_uvals);
@@ -189,6 +190,21 @@ cudaError_t Launch<T>::split_finish(vfpi_ctx* c, const void* partner_vstar) {
 }
 
 template <typename T>
+cudaError_t Launch<T>::block_sym_check(vfpi_ctx* c) {
+  if (c->n_pad > 0)
+    k_block_sym_check<T><<<blocks_for(c->n_pad, 128), 128, 0, c->stream>>>(dev_problem<T>(c), c->d_err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::make_vals6(vfpi_ctx* c) {
+  if (c->n_pad > 0)
+    k_make_vals6<T><<<blocks_for(c->n_pad, 128), 128, 0, c->stream>>>(dev_problem<T>(c),
+                                                                      static_cast<T*>(c->d_vals6));
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::to_internal(vfpi_ctx* c, const void* ext, void* internal) {
   if (c->N > 0)
     k_to_internal<T><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(
@@ -257,6 +273,26 @@ static void* grid_kernel(int nt, int minb, int pf, bool adj) {
   VFPI_GK(256, 2, 1) VFPI_GK(128, 4, 1) VFPI_GK(512, 1, 1) VFPI_GK(256, 2, 0)
 #undef VFPI_GK
   return nullptr;
+}
+
+// Grid-path kernels on the symmetric-block storage (forward sweeps; the
+// adjoint and Barzilai-Borwein steps read the full storage).
+template <typename T>
+static void* grid_kernel_b6(int nt, int minb) {
+  if (nt == 256 && minb == 3) return (void*)&k_solve_grid<T, 256, 3, false, false, false, true>;
+  if (nt == 256 && minb == 2) return (void*)&k_solve_grid<T, 256, 2, false, false, false, true>;
+  return nullptr;
+}
+
+template <typename T>
+static void* scenes_kernel_b6(int nt) {
+  switch (nt) {
+    case 64: return (void*)&k_solve_scenes<T, 64, false, true>;
+    case 128: return (void*)&k_solve_scenes<T, 128, false, true>;
+    case 256: return (void*)&k_solve_scenes<T, 256, false, true>;
+    case 512: return (void*)&k_solve_scenes<T, 512, false, true>;
+    default: return nullptr;
+  }
 }
 
 // Grid-path kernels on the symmetric storage.
@@ -407,6 +443,8 @@ static void* pick_kernel(vfpi_ctx* c, bool adj, size_t* smem) {
   }
   if (c->path == 1 && c->sym && c->sym_ok && !(!adj && c->bb_rule))
     return grid_kernel_sym<T>(c->nt, c->minb, adj);
+  if (c->b6 && c->bsym_ok && c->d_vals6 && !adj && !c->bb_rule)
+    return c->path == 1 ? grid_kernel_b6<T>(c->nt, c->minb) : scenes_kernel_b6<T>(c->nt);
   return c->path == 1 ? grid_kernel<T>(c->nt, c->minb, c->pf, adj) : scenes_kernel<T>(c->nt, adj);
 }
 
@@ -428,6 +466,14 @@ cudaError_t Launch<T>::configure(vfpi_ctx* c) {
       return e;
     int q = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, c->nt, smem)) != cudaSuccess) return e;
+    if (c->b6) {   // falls back to the full storage if a block stops being symmetric
+      int q2 = 0;
+      void* kf = c->path == 1 ? grid_kernel<T>(c->nt, c->minb, 0, adj != 0)
+                              : scenes_kernel<T>(c->nt, adj != 0);
+      if (!kf) return cudaErrorInvalidValue;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q2, kf, c->nt, 0)) != cudaSuccess) return e;
+      q = std::min(q, q2);
+    }
     if (c->path == 1 && c->sym) {   // falls back to the full storage if A stops being symmetric
       int q2 = 0;
       void* kf = grid_kernel<T>(c->nt, c->minb, 0, adj != 0);

@@ -26,9 +26,11 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "_lib", "tune_cache.json")
-GRID_VARIANTS = tuple(range(16)) + (26, 27)   # 12..15 need an exactly symmetric A
+# 12..15 need an exactly symmetric A, 28 and 29 (and the scene path's 30) symmetric blocks
+GRID_VARIANTS = tuple(range(16)) + (26, 27, 28, 29)
 WARPS = {0: 8, 1: 8, 2: 16, 3: 4, 4: 8, 5: 4, 6: 16, 7: 8, 8: 8, 9: 4, 10: 4, 11: 2,
-         12: 8, 13: 8, 14: 8, 15: 16, 26: 8, 27: 4}
+         12: 8, 13: 8, 14: 8, 15: 16, 26: 8, 27: 4, 28: 8, 29: 8}
+SCENE_B6 = 30
 CLUSTER_VARIANTS = tuple(range(16, 26))
 SPECIAL_MARGIN = 0.02
 
@@ -93,7 +95,7 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
         for var in GRID_VARIANTS:
             try:
                 solver.configure_launch(var, 0, 0)
-            except RuntimeError:    # symmetric storage needs A = A^T
+            except RuntimeError:    # symmetric storage / blocks need A = A^T / symmetric blocks
                 continue
             l2 = solver.layout()
             for g in _grid_candidates(l2["n_slices"], WARPS[var], l2["max_grid"], l2["sms"]):
@@ -107,11 +109,12 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
         # tolerance from the same warm start
         solver.set_tolerance(theta0, lmax0)
         v_start = solver.get_velocity()
-        shapes = [(0, bt) for bt in (64, 128, 256, 512)] + [(v, 0) for v in CLUSTER_VARIANTS]
+        shapes = [(v, bt) for v in (0, SCENE_B6) for bt in (64, 128, 256, 512)] + \
+            [(v, 0) for v in CLUSTER_VARIANTS]
         for var, bt in shapes:
             try:
                 solver.configure_launch(var, bt, 0)
-            except RuntimeError:    # shape not available on this GPU
+            except RuntimeError:    # shape not available (GPU, asymmetric blocks)
                 continue
             ms = _time(solver, sweeps, reps, v_start, before_rep)
             iters, _, _ = solver.status()
@@ -120,8 +123,9 @@ def tune(solver, sweeps: int = 20, reps: int = 3, cache: str | None = DEFAULT_CA
                                grid=solver.layout()["grid"]))
         solver.set_velocity(v_start)
     solver.set_tolerance(theta0, lmax0)
-    # the special kernels (TMA ring 8-11, symmetric storage 12-15, cluster
-    # 16-25) must beat the best plain shape by SPECIAL_MARGIN: a win inside
+    # the special kernels (TMA ring 8-11 and 26-27, symmetric storage 12-15,
+    # cluster 16-25, symmetric blocks 28-30) must beat the best plain shape by
+    # SPECIAL_MARGIN: a win inside
     # the timing noise should not switch kernels from one GPU to the next
     cost = lambda t: t.get("ms_per_solve", t["ms_per_sweep"])   # noqa: E731
     plain = [t for t in trials if t["kernel_variant"] < 8]

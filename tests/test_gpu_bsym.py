@@ -1,0 +1,69 @@
+"""Symmetric-block storage (launch variants 28, 29 and 30): when every 3x3
+block of A equals its transpose bit for bit, the forward kernels stream each
+block as its 6 distinct values and rebuild the same 9 entries, so the
+iterates must be bitwise those of the full storage.  Also: a matrix with an
+asymmetric block refuses the variants, and an update that makes a block
+asymmetric falls back to the full storage (and back again)."""
+import numpy as np
+import pytest
+
+from paper_2201_09212_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2201_09212_gb300 import vfpi  # noqa: E402
+
+
+def solve(sc, variant, block_threads=0, **kw):
+    with vfpi.Solver.from_scene(sc, **kw) as s:
+        s.configure_launch(variant, block_threads, 0)
+        r = s.solve(sc.v0)
+        return r, s.get_lambda()
+
+
+@pytest.mark.parametrize("bt", [64, 128, 256, 512])
+def test_batched_scenes_on_symmetric_blocks_equal_the_full_storage(bt):
+    sc = scenes.concat_scenes(scenes.batched_lattices(48, seed=17))
+    for kw in (dict(theta_th=-1.0, l_max=11), dict(theta_th=1e-6, l_max=300, norm="rms")):
+        ref, lref = solve(sc, 0, bt, force_path=2, **kw)
+        got, lgot = solve(sc, 30, bt, force_path=2, **kw)
+        assert np.array_equal(np.asarray(got.iters), np.asarray(ref.iters))
+        assert np.array_equal(got.v, ref.v) and np.array_equal(lgot, lref)
+
+
+def test_full_size_terrain_on_symmetric_blocks_equals_the_full_storage():
+    sc = scenes.terrain_lattice()
+    kw = dict(theta_th=1e-6, l_max=200, norm="rms", force_path=1)
+    ref, lref = solve(sc, 7, **kw)
+    for var in (28, 29):
+        got, lgot = solve(sc, var, **kw)
+        assert got.iters == ref.iters and np.array_equal(got.v, ref.v)
+        assert np.array_equal(lgot, lref)
+
+
+def test_asymmetric_blocks_refuse_the_variants_and_updates_fall_back():
+    fem = scenes.fem_block_scene(8, 8, 4, seed=1, dtype=np.float32)
+    with vfpi.Solver.from_scene(fem, force_path=1) as s:
+        for var in (28, 29):
+            with pytest.raises(vfpi.VfpiError) as x:
+                s.configure_launch(var, 0, 0)
+            assert x.value.status == vfpi.STATUS_CODES["VFPI_ERR_INVALID_ARG"]
+    # a lattice whose update makes one block asymmetric, then symmetric again
+    sc = scenes.terrain_lattice(dims=(40, 36, 6))
+    bad = sc.vals.copy()
+    k = int(np.nonzero(np.abs(bad[:, 0, 1]) > 0)[0][5])
+    bad[k, 0, 1] *= np.float32(1.0 + 2.0 ** -10)
+    kw = dict(theta_th=-1.0, l_max=9, force_path=1)
+    with vfpi.Solver.from_scene(sc, **kw) as s:
+        s.configure_launch(29, 0, 0)
+        for vals in (bad, sc.vals):
+            s.update(vals=vals)
+            r = s.solve(sc.v0)
+            with vfpi.Solver(sc.row_ptr, sc.col_idx, vals, sc.b, sc.node_i, sc.node_j, sc.R,
+                             sc.mu, sc.phi, h=sc.h, **kw) as full:
+                ref = full.solve(sc.v0)
+            assert np.array_equal(r.v, ref.v)

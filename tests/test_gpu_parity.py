@@ -354,7 +354,8 @@ def test_every_launch_variant_gives_identical_iterates():
     sc = scenes.terrain_lattice(dims=(40, 36, 6))
     ref = None
     with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=12, force_path=1) as s:
-        for var in list(range(16)) + [26, 27]:   # 12..15: symmetric storage; 26, 27: 2-stage rings
+        for var in list(range(16)) + [26, 27, 28, 29]:   # 12..15: symmetric storage; 26, 27:
+            # 2-stage rings; 28, 29: symmetric blocks
             for grid in (0, 17):
                 s.configure_launch(var, 0, grid)
                 r = s.solve(sc.v0)
@@ -383,7 +384,7 @@ def test_tma_and_register_shapes_agree_in_f64():
     sc = scenes.terrain_lattice(np.float64, dims=(40, 36, 6))
     ref = None
     with vfpi.Solver.from_scene(sc, theta_th=-1.0, l_max=12, force_path=1, dtype="f64") as s:
-        for var in (0, 7, 8, 9, 10, 11, 12, 26, 27):
+        for var in (0, 7, 8, 9, 10, 11, 12, 26, 27, 28, 29):
             s.configure_launch(var, 0, 0)
             r = s.solve(sc.v0)
             if ref is None:

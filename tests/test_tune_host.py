@@ -104,7 +104,7 @@ def test_refused_shapes_are_skipped_and_tolerance_restored():
     s = FakeSolver(1, grid_cost(1.0), refuse=range(12, 16))
     r = tune.tune(s, sweeps=10, reps=2, cache=None)
     tried = {t["kernel_variant"] for t in r["trials"]}
-    assert tried == set(range(12)) | {26, 27} and s.tol == (1e-6, 200)
+    assert tried == set(range(12)) | {26, 27, 28, 29} and s.tol == (1e-6, 200)
     assert set(s.tol_at_launch) == {(-1.0, 10)}          # fixed sweep count, no stop test
     assert all(t["ms_per_sweep"] == pytest.approx(grid_cost(1.0)(t["kernel_variant"], 0,
                                                                    t["grid_ctas"]) / 10)
@@ -138,7 +138,8 @@ def test_scene_path_times_whole_solves_and_restores_the_warm_start():
     v_start = s.get_velocity()
     r = tune.tune(s, sweeps=10, reps=2, cache=None)
     shapes = {(t["kernel_variant"], t["block_threads"]) for t in r["trials"]}
-    assert shapes == {(0, 64), (0, 128), (0, 256), (0, 512)} | {(v, 0) for v in range(16, 20)}
+    assert shapes == {(v, bt) for v in (0, 30) for bt in (64, 128, 256, 512)} | \
+        {(v, 0) for v in range(16, 20)}
     # every trial starts from the same warm start and is timed at the solver's tolerance
     assert all(t["ms_per_solve"] == pytest.approx(t["ms_per_sweep"] * 20) for t in r["trials"])
     assert set(s.tol_at_launch) == {(1e-6, 200)}
