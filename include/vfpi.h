@@ -198,8 +198,8 @@ enum {
    * bit for bit (checked whenever A is set; a mass-spring lattice's blocks
    * are): each block streams as its 6 distinct values, 24 + 4 instead of
    * 36 + 4 bytes, rebuilt to the same 9 entries and FMAs, so the iterates are
-   * bitwise those of the full storage.  Forward solves only (the adjoint and
-   * Barzilai-Borwein steps read the full storage); if a later vfpi_update
+   * bitwise those of the full storage.  Forward and adjoint solves
+   * (Barzilai-Borwein steps read the full storage); if a later vfpi_update
    * makes a block asymmetric, solves fall back to the full storage.  The
    * 6-value copy (24 bytes per stored slot) is built when the variant is
    * chosen.  Grid path: VFPI_VARIANT_DEFAULT's and VFPI_VARIANT_256_2's

@@ -275,22 +275,27 @@ static void* grid_kernel(int nt, int minb, int pf, bool adj) {
   return nullptr;
 }
 
-// Grid-path kernels on the symmetric-block storage (forward sweeps; the
-// adjoint and Barzilai-Borwein steps read the full storage).
+// Grid-path and scene kernels on the symmetric-block storage (the forward
+// sweep, and the adjoint's, which is the forward product with b := g_v on the
+// symmetric A; Barzilai-Borwein steps read the full storage).
 template <typename T>
-static void* grid_kernel_b6(int nt, int minb) {
-  if (nt == 256 && minb == 3) return (void*)&k_solve_grid<T, 256, 3, false, false, false, true>;
-  if (nt == 256 && minb == 2) return (void*)&k_solve_grid<T, 256, 2, false, false, false, true>;
+static void* grid_kernel_b6(int nt, int minb, bool adj) {
+#define VFPI_GB(NT_, MB_)                                                               \
+  if (nt == NT_ && minb == MB_)                                                         \
+    return adj ? (void*)&k_solve_grid<T, NT_, MB_, false, true, false, true>            \
+               : (void*)&k_solve_grid<T, NT_, MB_, false, false, false, true>;
+  VFPI_GB(256, 3) VFPI_GB(256, 2)
+#undef VFPI_GB
   return nullptr;
 }
 
 template <typename T>
-static void* scenes_kernel_b6(int nt) {
+static void* scenes_kernel_b6(int nt, bool adj) {
   switch (nt) {
-    case 64: return (void*)&k_solve_scenes<T, 64, false, true>;
-    case 128: return (void*)&k_solve_scenes<T, 128, false, true>;
-    case 256: return (void*)&k_solve_scenes<T, 256, false, true>;
-    case 512: return (void*)&k_solve_scenes<T, 512, false, true>;
+    case 64: return adj ? (void*)&k_solve_scenes<T, 64, true, true> : (void*)&k_solve_scenes<T, 64, false, true>;
+    case 128: return adj ? (void*)&k_solve_scenes<T, 128, true, true> : (void*)&k_solve_scenes<T, 128, false, true>;
+    case 256: return adj ? (void*)&k_solve_scenes<T, 256, true, true> : (void*)&k_solve_scenes<T, 256, false, true>;
+    case 512: return adj ? (void*)&k_solve_scenes<T, 512, true, true> : (void*)&k_solve_scenes<T, 512, false, true>;
     default: return nullptr;
   }
 }
@@ -443,8 +448,8 @@ static void* pick_kernel(vfpi_ctx* c, bool adj, size_t* smem) {
   }
   if (c->path == 1 && c->sym && c->sym_ok && !(!adj && c->bb_rule))
     return grid_kernel_sym<T>(c->nt, c->minb, adj);
-  if (c->b6 && c->bsym_ok && c->d_vals6 && !adj && !c->bb_rule)
-    return c->path == 1 ? grid_kernel_b6<T>(c->nt, c->minb) : scenes_kernel_b6<T>(c->nt);
+  if (c->b6 && c->bsym_ok && c->d_vals6 && !(!adj && c->bb_rule))
+    return c->path == 1 ? grid_kernel_b6<T>(c->nt, c->minb, adj) : scenes_kernel_b6<T>(c->nt, adj);
   return c->path == 1 ? grid_kernel<T>(c->nt, c->minb, c->pf, adj) : scenes_kernel<T>(c->nt, adj);
 }
 

@@ -67,3 +67,23 @@ def test_asymmetric_blocks_refuse_the_variants_and_updates_fall_back():
                              sc.mu, sc.phi, h=sc.h, **kw) as full:
                 ref = full.solve(sc.v0)
             assert np.array_equal(r.v, ref.v)
+
+
+@pytest.mark.parametrize("path,var_full,var_b6", [(2, 0, 30), (1, 7, 29)])
+def test_adjoint_on_symmetric_blocks_equals_the_full_storage(path, var_full, var_b6):
+    """The adjoint sweep is the forward product with b := g_v (A is
+    symmetric): on the 6-value blocks it gives dL/db, dL/dphi and dL/dmu bit
+    for bit as on the full storage."""
+    sc = (scenes.concat_scenes(scenes.batched_lattices(24, seed=23)) if path == 2
+          else scenes.terrain_lattice(dims=(40, 36, 6)))
+    g_v = np.random.default_rng(5).standard_normal(sc.n).astype(np.float32)
+    out = []
+    for var in (var_full, var_b6):
+        with vfpi.Solver.from_scene(sc, theta_th=1e-6, l_max=300, norm="rms",
+                                    force_path=path) as s:
+            s.configure_launch(var, 256 if path == 2 else 0, 0)
+            s.solve(sc.v0)
+            out.append(s.adjoint(g_v))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(np.asarray(out[0][3]), np.asarray(out[1][3]))
