@@ -338,7 +338,7 @@ __device__ __forceinline__ void expand6(const T (&q)[6], T (&m)[9]) {
   m[6] = q[2]; m[7] = q[4]; m[8] = q[5];
 }
 
-template <typename T>
+template <typename T, int UNR = 1>
 __device__ __forceinline__ void row_product6(const DevProblem<T>& P, int slice, int lane,
                                              const Vec4<T>* vin, T& a0, T& a1, T& a2) {
   constexpr int VW = Chunk<T>::VW;
@@ -348,8 +348,9 @@ __device__ __forceinline__ void row_product6(const DevProblem<T>& P, int slice, 
   const int32_t* __restrict__ cb = P.cols + off * 32;
   a0 = T(0); a1 = T(0); a2 = T(0);
   const int nfull = len / VW;
-#pragma unroll 1
-  for (int k = 0; k < nfull; ++k) {
+  // UNR = 2: two chunks per iteration, so that the second chunk's loads are in
+  // flight during the first one's FMAs (where the register budget allows)
+  auto chunk = [&](int k) {
     int c[VW];
     T q[6][VW];
     Chunk<T>::cols(cb + (int64_t)k * (32 * VW) + lane * VW, c);
@@ -367,6 +368,13 @@ __device__ __forceinline__ void row_product6(const DevProblem<T>& P, int slice, 
       a1 = fma(m[3], x.x, fma(m[4], x.y, fma(m[5], x.z, a1)));
       a2 = fma(m[6], x.x, fma(m[7], x.y, fma(m[8], x.z, a2)));
     }
+  };
+  if constexpr (UNR == 2) {
+#pragma unroll 2
+    for (int k = 0; k < nfull; ++k) chunk(k);
+  } else {
+#pragma unroll 1
+    for (int k = 0; k < nfull; ++k) chunk(k);
   }
   const int ntail = len - nfull * VW;
   const T* pt = vb + (int64_t)nfull * (192 * VW) + lane;
@@ -742,12 +750,12 @@ __device__ __forceinline__ double finish_row(const DevProblem<T>& P, int row, T 
                                  ldv(P.w + row), __ldg(P.cslot + row), vout + row, ch);
 }
 
-template <typename T, bool ADJ, bool PF = false, bool SYM = false, bool B6 = false>
+template <typename T, bool ADJ, bool PF = false, bool SYM = false, bool B6 = false, int U6 = 1>
 __device__ __forceinline__ double sweep_row(const DevProblem<T>& P, int slice, int lane,
                                             const Vec4<T>* vin, Vec4<T>* vout,
                                             const ChebStep<T>& ch) {
   T a0, a1, a2;
-  if constexpr (B6) row_product6(P, slice, lane, vin, a0, a1, a2);
+  if constexpr (B6) row_product6<T, U6>(P, slice, lane, vin, a0, a1, a2);
   else if constexpr (SYM) row_product_sym(P, slice, lane, vin, a0, a1, a2);
   else if constexpr (PF) row_product_prefetch(P, slice, lane, vin, a0, a1, a2);
   else row_product(P, slice, lane, vin, a0, a1, a2);
@@ -1137,7 +1145,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       }
     } else {
       for (int s = gw; s < P.n_slices; s += nw)
-        acc += sweep_row<T, ADJ, PF, SYM, B6>(P, s, lane, vin, vout, ch);
+        acc += sweep_row<T, ADJ, PF, SYM, B6, (MINB <= 2 ? 2 : 1)>(P, s, lane, vin, vout, ch);
       if (ctl.n_d > 0) {
         if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
@@ -1485,7 +1493,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
         }
       } else {
         for (int s = s0 + wid; s < s1; s += NT / 32)
-          acc += sweep_row<T, ADJ, false, false, B6>(P, s, lane, vin, vout, ch);
+          acc += sweep_row<T, ADJ, false, false, B6, 2>(P, s, lane, vin, vout, ch);
         if (d1 > d0) {
           __syncthreads();
           for (int d = d0 + threadIdx.x; d < d1; d += NT)
