@@ -410,6 +410,8 @@ def batched_bench(args, torch, dev, stream, rank):
                  " on symmetric blocks (6 values per block streamed; effective fraction)"
                  if var == 30 else ""))
     tr_key = (source_hash(), "b6" if var == 30 else "full", threads)
+    tr_ratio = (NCU_BATCH_TRAFFIC[tr_key][0] / NCU_BATCH_TRAFFIC[tr_key][1]
+                if tr_key in NCU_BATCH_TRAFFIC and (var < 16 or var == 30) else None)
     s.close()
     return {
         "workload": f"{S} lattices, side U{{4..12}}, {int(nq.sum()) * 3} DOF, {sc.nnzb} blocks, {sc.n_c} contacts",
@@ -418,9 +420,10 @@ def batched_bench(args, torch, dev, stream, rank):
         "iters_per_scene": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
         "solve_kernel": {"name": kname, "ms_avg": 1e3 * k_avg,
                          "achieved_gbs": alg / k_avg / 1e9, "frac": alg / k_avg / 1e9 / peaks()[0],
-                         "traffic_over_algorithmic": (
-                             NCU_BATCH_TRAFFIC[tr_key][0] / NCU_BATCH_TRAFFIC[tr_key][1]
-                             if tr_key in NCU_BATCH_TRAFFIC and (var < 16 or var == 30) else None)},
+                         "traffic_over_algorithmic": tr_ratio,
+                         # DRAM bytes actually moved (ncu ratio x algorithmic) over the live time
+                         "dram_frac": (tr_ratio * alg / k_avg / 1e9 / peaks()[0]
+                                       if tr_ratio else None)},
         "graph": "one CUDA graph per env step (harness, warm start, solve, integrate)",
         "layout": {"blocks": int(sc.nnzb), "stored_slots": int(lay_b["slots"]),
                    "padding": lay_b["slots"] / sc.nnzb - 1.0},
@@ -793,6 +796,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": (tr * it_avg if tr else None),
+                # the DRAM bytes the kernel moves (ncu, per launch) over its live time:
+                # below frac where v, b, W hit L2, far below it on the 6-value blocks
+                "dram_frac": (tr * it_avg / k_avg / 1e9 / peak if tr else None),
                 "algorithmic_bytes_per_sweep": bps,
                 "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
                           + (" (symmetric storage; effective fraction)" if sym else "")
