@@ -46,13 +46,13 @@ ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under
 # kernel, keyed by (hash of the CUDA sources it was captured from, kernel
 # variant), each captured at the variant's default CTA count; stale entries
 # read as null (the grid kernel's ncu summary gives the captures)
-NCU_TRAFFIC = {("3049347651bdea7e", 0): 554559173, ("3049347651bdea7e", 7): 553443487,
-               ("3049347651bdea7e", 28): 388317140, ("3049347651bdea7e", 29): 387861710}
+NCU_TRAFFIC = {("f1c078f9dd091872", 0): 554690646, ("f1c078f9dd091872", 7): 553545912,
+               ("f1c078f9dd091872", 28): 388424784, ("f1c078f9dd091872", 29): 387908524}
 # the same for the batched kernel: (DRAM read + write bytes, algorithmic bytes)
 # of one captured env-step solve launch (the bench's launch log gives the
 # captured launch's own count), keyed by (source hash, "full" or "b6" storage,
 # threads per CTA)
-NCU_BATCH_TRAFFIC = {("3049347651bdea7e", "b6", 128): (118874947000, 172972435132)}
+NCU_BATCH_TRAFFIC = {("f1c078f9dd091872", "b6", 256): (114015485952, 172972435132)}
 
 
 def source_hash() -> str:
