@@ -50,9 +50,15 @@ NCU_TRAFFIC = {("f1c078f9dd091872", 0): 554690646, ("f1c078f9dd091872", 7): 5535
                ("f1c078f9dd091872", 28): 388424784, ("f1c078f9dd091872", 29): 387908524}
 # the same for the batched kernel: (DRAM read + write bytes, algorithmic bytes)
 # of one captured env-step solve launch (the bench's launch log gives the
-# captured launch's own count), keyed by (source hash, "full" or "b6" storage,
-# threads per CTA)
-NCU_BATCH_TRAFFIC = {("f1c078f9dd091872", "b6", 256): (114015485952, 172972435132)}
+# captured launch's own count), keyed by (source hash, storage of A as
+# Solver.storage() names it, threads per CTA)
+NCU_BATCH_TRAFFIC = {("f1c078f9dd091872", "blocks6", 256): (114015485952, 172972435132)}
+# kernel-name notes for the compressed storages of A (the fraction keeps the
+# 40-byte full-BSR count per block, so on these it is an effective one)
+STORAGE_NOTE = {
+    "symmetric": " (symmetric storage; effective fraction)",
+    "blocks6": " on symmetric blocks (6 values per block streamed; effective fraction)",
+}
 
 
 def source_hash() -> str:
@@ -403,13 +409,12 @@ def batched_bench(args, torch, dev, stream, rank):
     per_scene_total = float(np.mean(per_ms)) / 1e3 * S
     first_batch = kms[0] / 1e3
     lay_b = s.layout()
+    stor_b = s.storage()["storage"]
     threads = lay_b["threads"]
     var = int(tuned.get("kernel_variant", 0))
     kname = (f"k_solve_cluster<float,{threads}> (launch shape {var})" if 16 <= var <= 25
-             else f"k_solve_scenes<float,{threads}>" + (
-                 " on symmetric blocks (6 values per block streamed; effective fraction)"
-                 if var == 30 else ""))
-    tr_key = (source_hash(), "b6" if var == 30 else "full", threads)
+             else f"k_solve_scenes<float,{threads}>" + STORAGE_NOTE.get(stor_b, ""))
+    tr_key = (source_hash(), stor_b, threads)
     tr_ratio = (NCU_BATCH_TRAFFIC[tr_key][0] / NCU_BATCH_TRAFFIC[tr_key][1]
                 if tr_key in NCU_BATCH_TRAFFIC and (var < 16 or var == 30) else None)
     s.close()
@@ -674,6 +679,7 @@ def main():
     else:
         tuned = tune.tune(s, sweeps=30, reps=3)  # launch shape (cached per layout and GPU)
     lay = s.layout()
+    stor = s.storage()["storage"]
     dev = torch.device("cuda", local)
     v0 = torch.from_numpy(sc.v0).to(dev)
     x = torch.from_numpy(sc.x0).to(dev)
@@ -783,8 +789,6 @@ def main():
             dist.destroy_process_group()
         return
 
-    sym = 12 <= int(tuned["kernel_variant"]) <= 15
-    b6 = int(tuned["kernel_variant"]) in (28, 29)
     # always the full-BSR count: a compressed storage is reported as an
     # effective fraction next to the measured DRAM bytes, not by a new count
     bps = algorithmic_bytes_per_sweep(sc)
@@ -801,9 +805,7 @@ def main():
                 "dram_frac": (tr * it_avg / k_avg / 1e9 / peak if tr else None),
                 "algorithmic_bytes_per_sweep": bps,
                 "kernel": f"k_solve_grid<float,{lay['threads']}> variant {tuned['kernel_variant']}"
-                          + (" (symmetric storage; effective fraction)" if sym else "")
-                          + (" (symmetric blocks: 6 values per block streamed, the 40-byte"
-                             " full-BSR count kept; effective fraction)" if b6 else ""),
+                          + STORAGE_NOTE.get(stor, ""),
                 "kernel_ms_avg": 1e3 * k_avg}
     cpu = cpu_all = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -829,8 +831,9 @@ def main():
                               "threads": lay["threads"], "tuned_ms_per_sweep": tuned["ms_per_sweep"],
                               "from_cache": tuned["cached"]},
                    "l2": ("inputs larger than L2 (" + (
-                       f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks" if sym
-                       else f"{sc.nnzb * 28 / 1e6:.0f} MB of 6-value blocks" if b6
+                       f"{((sc.nnzb + sc.n_nodes) // 2) * 40 / 1e6:.0f} MB of upper blocks"
+                       if stor == "symmetric"
+                       else f"{sc.nnzb * 28 / 1e6:.0f} MB of 6-value blocks" if stor == "blocks6"
                        else f"{sc.nnzb * 40 / 1e6:.0f} MB of blocks") + " streamed per sweep)")},
         "roofline": roofline,
         "time_to_solution": time_to_solution,

@@ -312,6 +312,15 @@ vfpi_status vfpi_last_kernel_ms(vfpi_t ctx, float* ms);
  * be resident at once, [7] SMs of the device. */
 vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info8);
 
+/* How the solve kernels read A (no work on the device): info4[0] the storage
+ * of the forward sweep in the current launch shape -- 0 the full 3x3 blocks
+ * (36 + 4 bytes per block), 1 the symmetric storage (upper blocks, grid
+ * path), 2 the symmetric-block storage (6 values per block, 24 + 4 bytes);
+ * [1] every stored block is symmetric bit for bit; [2] A is symmetric (grid
+ * path); [3] 0.  The iterates are bitwise those of the full storage in every
+ * case. */
+vfpi_status vfpi_get_storage(vfpi_t ctx, int32_t* info4);
+
 /* Replace theta_th and l_max of Alg. 1 for later solves (and the adjoint). */
 vfpi_status vfpi_set_tolerance(vfpi_t ctx, double theta_th, int32_t l_max);
 

@@ -1389,6 +1389,21 @@ vfpi_status vfpi_get_layout(vfpi_t c, int64_t* info) {
   return VFPI_OK;
 }
 
+vfpi_status vfpi_get_storage(vfpi_t c, int32_t* info) {
+  CTX_CHECK(c);
+  if (!info) return arg_fail(c, VFPI_ERR_INVALID_ARG, "info is NULL");
+  int st = 0;
+  if (c->path == 2 && c->cluster > 0) st = 0;
+  else if (c->path == 1 && c->tma_stages > 0) st = 0;
+  else if (c->path == 1 && c->sym && c->sym_ok) st = 1;
+  else if (c->b6 && c->bsym_ok && c->d_vals6) st = 2;
+  info[0] = st;
+  info[1] = c->bsym_ok;
+  info[2] = c->sym_ok;
+  info[3] = 0;
+  return VFPI_OK;
+}
+
 vfpi_status vfpi_set_regularization(vfpi_t c, const void* omega) {
   CTX_CHECK(c);
   if (c->n_c == 0) return VFPI_OK;

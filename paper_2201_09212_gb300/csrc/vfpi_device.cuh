@@ -349,7 +349,9 @@ __device__ __forceinline__ void row_product6(const DevProblem<T>& P, int slice, 
   a0 = T(0); a1 = T(0); a2 = T(0);
   const int nfull = len / VW;
   // UNR = 2: two chunks per iteration, so that the second chunk's loads are in
-  // flight during the first one's FMAs (where the register budget allows)
+  // flight during the first one's FMAs (where the register budget allows; the
+  // adjoint sweeps keep one chunk: two made the batched adjoint solve 10 %
+  // slower)
   auto chunk = [&](int k) {
     int c[VW];
     T q[6][VW];
@@ -1145,7 +1147,7 @@ __global__ void __launch_bounds__(NT, MINB) k_solve_grid(DevProblem<T> P, SolveC
       }
     } else {
       for (int s = gw; s < P.n_slices; s += nw)
-        acc += sweep_row<T, ADJ, PF, SYM, B6, (MINB <= 2 ? 2 : 1)>(P, s, lane, vin, vout, ch);
+        acc += sweep_row<T, ADJ, PF, SYM, B6, (!ADJ && MINB <= 2 ? 2 : 1)>(P, s, lane, vin, vout, ch);
       if (ctl.n_d > 0) {
         if (!grid_barrier(ctl.bar, nbar, &s_ok)) { st = ST_TIMEOUT; break; }
         for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
@@ -1493,7 +1495,7 @@ __global__ void __launch_bounds__(NT) k_solve_scenes(DevProblem<T> P, SolveCtl c
         }
       } else {
         for (int s = s0 + wid; s < s1; s += NT / 32)
-          acc += sweep_row<T, ADJ, false, false, B6, 2>(P, s, lane, vin, vout, ch);
+          acc += sweep_row<T, ADJ, false, false, B6, ADJ ? 1 : 2>(P, s, lane, vin, vout, ch);
         if (d1 > d0) {
           __syncthreads();
           for (int d = d0 + threadIdx.x; d < d1; d += NT)

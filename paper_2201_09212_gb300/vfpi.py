@@ -32,7 +32,7 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
             "vfpi_get_scene_status",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
-            "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
+            "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout", "vfpi_get_storage",
             "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
             "vfpi_set_adjoint_chebyshev", "vfpi_set_adjoint_tolerance",
             "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
@@ -115,6 +115,7 @@ def lib():
         "vfpi_set_anisotropic_friction": (st, [vp, vp]),
         "vfpi_set_barzilai_borwein": (st, [vp, i32, C.c_double]),
         "vfpi_get_layout": (st, [vp, vp]),
+        "vfpi_get_storage": (st, [vp, vp]),
         "vfpi_last_error": (C.c_char_p, [vp]),
         "vfpi_status_string": (C.c_char_p, [st]),
         "vfpi_destroy": (None, [vp]),
@@ -514,3 +515,14 @@ class Solver:
         self._check(self._L.vfpi_get_layout(self._h, info))
         keys = ("n_pad", "n_slices", "slots", "path", "grid", "threads", "max_grid", "sms")
         return dict(zip(keys, (int(x) for x in info)))
+
+    STORAGE_NAMES = ("full", "symmetric", "blocks6")
+
+    def storage(self) -> dict:
+        """How the solve kernels read A: the forward sweep's storage in the
+        current launch shape (``full``, ``symmetric`` or ``blocks6``) and the
+        flags that allow the others."""
+        info = (C.c_int32 * 4)()
+        self._check(self._L.vfpi_get_storage(self._h, info))
+        return {"storage": self.STORAGE_NAMES[int(info[0])], "blocks_symmetric": bool(info[1]),
+                "a_symmetric": bool(info[2])}
