@@ -741,12 +741,8 @@ def main():
     v_out = torch.empty_like(v_h).pin_memory()
     e2e_iters = []
 
-    def e2e_step():
-        s.set_rhs(b_h, phi_h)
-        v_out.copy_(v_h)
-        r = s.solve(v_out, out_v=v_out, out_lam=lam_h)
-        s.integrate(x_h)
-        return r
+    def e2e_step():   # one call per time step: inputs up, solve, outputs down, x integrated
+        return s.advance(b_h, phi_h, v_h, out_v=v_out, out_lam=lam_h, x=x_h)
 
     for _ in range(args.warmup):
         e2e_step()

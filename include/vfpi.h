@@ -291,6 +291,23 @@ vfpi_status vfpi_adjoint(vfpi_t ctx, const void* lambda_star, const void* g_v, v
  * x_inout [3N] double. */
 vfpi_status vfpi_integrate(vfpi_t ctx, double* x_inout);
 
+/* One time step (eq. disc_dyn) in one call: b [3N] and phi [n_c] as
+ * vfpi_set_rhs, warm start v_start [3N] as vfpi_set_velocity, Alg. 1 as
+ * vfpi_solve, v_out [3N] = v_hat and lambda_out [3n_c] as vfpi_get_velocity /
+ * vfpi_get_lambda, then x_inout [3N] double += h v_hat as vfpi_integrate.
+ * Every pointer is nullable (NULL: that input keeps its current value, that
+ * output is not written) and may be host or device memory; v_start and v_out
+ * may be the same array.  The copies and kernels are queued back to back on
+ * the context's stream -- the positions' upload on a side stream, overlapping
+ * the solve -- and the call waits once, at the end, so page-locked host
+ * arrays may be changed when it returns.  Results are bitwise those of the
+ * separate calls.  Returns as vfpi_solve; VFPI_ERR_INVALID_ARG inside a
+ * stream capture (the call waits; capture vfpi_solve_async instead),
+ * VFPI_ERR_UNSUPPORTED on a shard. */
+vfpi_status vfpi_advance(vfpi_t ctx, const void* b, const void* phi, const void* v_start,
+                         void* v_out, void* lambda_out, double* x_inout, int32_t* iters_out,
+                         double* theta_out);
+
 /* y = A x with the context's A (x, y [3N]); the only super-linear product of
  * the method (Sec. III.F), exposed for residual checks and dynamics harnesses. */
 vfpi_status vfpi_matvec(vfpi_t ctx, const void* x, void* y);

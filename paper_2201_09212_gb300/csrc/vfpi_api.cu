@@ -71,6 +71,7 @@ cudaError_t ensure_stage(vfpi_ctx* c, size_t bytes) {
   if (bytes <= c->stage_bytes) return cudaSuccess;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return e;
+  if (c->aux_stream && (e = cudaStreamSynchronize(c->aux_stream)) != cudaSuccess) return e;
   if (c->d_stage) cudaFree(c->d_stage);
   c->d_stage = nullptr;
   c->stage_bytes = 0;
@@ -108,6 +109,21 @@ cudaError_t device_view(vfpi_ctx* c, const void* src, size_t bytes, size_t slot,
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(c->stream, &cap)) != cudaSuccess) return e;
   return cap == cudaStreamCaptureStatusNone ? cudaStreamSynchronize(c->stream) : cudaSuccess;
+}
+
+// The same view without the wait for page-locked sources, queued on stream
+// `s`: for a call that waits for its whole step before it returns.  The
+// staging buffer must already hold slot + bytes.
+cudaError_t device_view_queued(vfpi_ctx* c, const void* src, size_t bytes, size_t slot,
+                               cudaStream_t s, const void** out) {
+  if (on_device(src)) {
+    *out = src;
+    return cudaSuccess;
+  }
+  char* dst = static_cast<char*>(c->d_stage) + slot;
+  *out = dst;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
 }
 
 // Write `bytes` of device data to caller memory (host or device).
@@ -148,6 +164,9 @@ void free_all(vfpi_ctx* c) {
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev_main) cudaEventDestroy(c->ev_main);
+  if (c->ev_aux) cudaEventDestroy(c->ev_aux);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -1294,6 +1313,84 @@ vfpi_status vfpi_solve(vfpi_t c, void* v_inout, void* lambda_out, int32_t* iters
   if (v_inout && (st = vfpi_get_velocity(c, v_inout)) != VFPI_OK) return st;
   if (lambda_out && (st = vfpi_get_lambda(c, lambda_out)) != VFPI_OK) return st;
   return run;
+}
+
+vfpi_status vfpi_advance(vfpi_t c, const void* b, const void* phi, const void* v_start,
+                         void* v_out, void* lambda_out, double* x, int32_t* iters_out,
+                         double* theta_out) {
+  CTX_CHECK(c);
+  NOT_ON_SHARD(c, "vfpi_advance (use vfpi_shard_sweep)");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  VFPI_TRY_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return arg_fail(c, VFPI_ERR_INVALID_ARG,
+                    "vfpi_advance waits for its step; inside a stream capture use vfpi_solve_async");
+  const size_t vb = c->esz * 3 * (size_t)c->N, pb = c->esz * (size_t)c->n_c;
+  const size_t lb = 3 * pb, xb = 8 * 3 * (size_t)c->N;
+  // every staging slot is sized first: growing the buffer invalidates views
+  size_t top = 0;
+  auto slot = [&](size_t bytes) {
+    const size_t at = top;
+    top += round_up(bytes, 256);
+    return at;
+  };
+  const size_t s_b = slot(vb), s_phi = slot(pb), s_v = slot(vb), s_x = slot(xb);
+  const size_t s_vo = slot(vb), s_l = slot(lb);
+  VFPI_TRY_CUDA(ensure_stage(c, top));
+  cudaStream_t st = c->stream;
+  // the positions go up on the side stream, after the stream's earlier work
+  // (which may still read the staging buffer), while the solve runs
+  double* xdev = x;
+  const bool x_staged = x && !on_device(x) && xb > 0;
+  if (x_staged) {
+    if (!c->aux_stream) {
+      VFPI_TRY_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+      VFPI_TRY_CUDA(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
+      VFPI_TRY_CUDA(cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
+    }
+    VFPI_TRY_CUDA(cudaEventRecord(c->ev_main, st));
+    VFPI_TRY_CUDA(cudaStreamWaitEvent(c->aux_stream, c->ev_main, 0));
+    const void* dx;
+    VFPI_TRY_CUDA(device_view_queued(c, x, xb, s_x, c->aux_stream, &dx));
+    VFPI_TRY_CUDA(cudaEventRecord(c->ev_aux, c->aux_stream));
+    xdev = const_cast<double*>(static_cast<const double*>(dx));
+  }
+  if (b) {
+    const void* db;
+    VFPI_TRY_CUDA(device_view_queued(c, b, vb, s_b, st, &db));
+    VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, db, c->d_b)));
+  }
+  if (phi && pb > 0) {
+    const void* dp;
+    VFPI_TRY_CUDA(device_view_queued(c, phi, pb, s_phi, st, &dp));
+    VFPI_TRY_CUDA(DISPATCH(c, contact_scalar(c, dp, c->d_cphi, false)));
+  }
+  if (v_start) {
+    const void* dv;
+    VFPI_TRY_CUDA(device_view_queued(c, v_start, vb, s_v, st, &dv));
+    VFPI_TRY_CUDA(DISPATCH(c, to_internal(c, dv, c->d_v0)));
+  }
+  VFPI_TRY_CUDA(DISPATCH(c, solve(c, c->opts.l_max, c->opts.theta_th, false)));
+  if (v_out) {
+    void* dst;
+    VFPI_TRY_CUDA(out_view(c, v_out, vb, s_vo, &dst));
+    VFPI_TRY_CUDA(DISPATCH(c, to_external(c, c->d_v0, dst)));
+    if (dst != v_out) VFPI_TRY_CUDA(cudaMemcpyAsync(v_out, dst, vb, cudaMemcpyDeviceToHost, st));
+  }
+  if (lambda_out && lb > 0) {
+    void* dst;
+    VFPI_TRY_CUDA(out_view(c, lambda_out, lb, s_l, &dst));
+    VFPI_TRY_CUDA(DISPATCH(c, lambda_external(c, c->d_lam, dst)));
+    if (dst != lambda_out)
+      VFPI_TRY_CUDA(cudaMemcpyAsync(lambda_out, dst, lb, cudaMemcpyDeviceToHost, st));
+  }
+  if (x) {
+    if (x_staged) VFPI_TRY_CUDA(cudaStreamWaitEvent(st, c->ev_aux, 0));
+    VFPI_TRY_CUDA(DISPATCH(c, integrate(c, xdev)));
+    if (x_staged) VFPI_TRY_CUDA(cudaMemcpyAsync(x, xdev, xb, cudaMemcpyDeviceToHost, st));
+  }
+  // the one wait: the status words come back behind everything above
+  return vfpi_get_status(c, iters_out, theta_out);
 }
 
 vfpi_status vfpi_integrate(vfpi_t c, double* x) {

@@ -153,6 +153,10 @@ struct vfpi_ctx {
   int max_grid = 0;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // vfpi_advance: a side stream for the positions' upload, which overlaps the
+  // solve (created on first use)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_aux = nullptr;
   bool timed = false;
   std::string err;
 };

@@ -32,7 +32,8 @@ EXPORTED = ("vfpi_default_opts", "vfpi_create", "vfpi_update", "vfpi_set_rhs",
             "vfpi_step", "vfpi_solve", "vfpi_solve_async", "vfpi_get_status",
             "vfpi_get_scene_status",
             "vfpi_get_lambda_star", "vfpi_set_friction", "vfpi_adjoint",
-            "vfpi_integrate", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout", "vfpi_get_storage",
+            "vfpi_integrate", "vfpi_advance", "vfpi_matvec", "vfpi_last_kernel_ms", "vfpi_get_layout",
+            "vfpi_get_storage",
             "vfpi_configure_launch", "vfpi_set_tolerance", "vfpi_set_chebyshev",
             "vfpi_set_adjoint_chebyshev", "vfpi_set_adjoint_tolerance",
             "vfpi_set_regularization", "vfpi_set_anisotropic_friction",
@@ -104,6 +105,7 @@ def lib():
         "vfpi_get_status": (st, [vp, vp, vp]),
         "vfpi_get_scene_status": (st, [vp, vp]),
         "vfpi_integrate": (st, [vp, vp]),
+        "vfpi_advance": (st, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "vfpi_matvec": (st, [vp, vp, vp]),
         "vfpi_last_kernel_ms": (st, [vp, vp]),
         "vfpi_configure_launch": (st, [vp, i32, i32, i32]),
@@ -465,6 +467,29 @@ class Solver:
             raise TypeError("x must be a contiguous float64 array")
         self._check(self._L.vfpi_integrate(self._h, x.ctypes.data))
         return x
+
+    def advance(self, b=None, phi=None, v=None, out_v=None, out_lam=None, x=None) -> SolveResult:
+        """One time step in one call (vfpi_advance): right-hand side ``b``/``phi``,
+        warm start ``v``, Alg. 1, ``out_v``/``out_lam`` written, ``x`` (FP64,
+        updated in place) integrated; one wait for the whole step.  Outputs
+        are allocated as host arrays when not given."""
+        k = _Keep()
+        if x is not None and not _is_torch(x) and not (
+                isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+            raise TypeError("x must be a contiguous float64 array")
+        vo = self._out(self.n, out_v)
+        lam = self._out(3 * self.n_c, out_lam)
+        iters = np.zeros(self.n_scenes, dtype=np.int32)
+        theta = np.zeros(self.n_scenes, dtype=np.float64)
+        st = self._L.vfpi_advance(self._h, k.ptr(b, self.np_dtype), k.ptr(phi, self.np_dtype),
+                                  k.ptr(v, self.np_dtype), k.ptr(vo, self.np_dtype),
+                                  k.ptr(lam, self.np_dtype),
+                                  None if x is None else k.ptr(x, np.float64),
+                                  iters.ctypes.data, theta.ctypes.data)
+        self._check(st, allow_nc=True)
+        if self.n_scenes == 1:
+            return SolveResult(vo, lam, int(iters[0]), float(theta[0]), st)
+        return SolveResult(vo, lam, iters, theta, st)
 
     def matvec(self, x, out=None):
         out = self._out(self.n, out)
