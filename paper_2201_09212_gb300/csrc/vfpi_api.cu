@@ -152,7 +152,7 @@ void free_all(vfpi_ctx* c) {
   void* ptrs[] = {c->d_slice_len, c->d_slice_off, c->d_slice_cmin, c->d_slice_cmax, c->d_vals, c->d_cols, c->d_b, c->d_w,
                   c->d_v0, c->d_v1, c->d_t0, c->d_t1, c->d_cslot, c->d_node_map, c->d_row_ptr, c->d_ds,
                   c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2,
-                  c->d_lam, c->d_lam_star, c->d_dstar, c->d_scene_slice, c->d_scene_d, c->d_order,
+                  c->d_lam, c->d_lam_star, c->d_lam2, c->d_lam_star2, c->d_dstar, c->d_scene_slice, c->d_scene_d, c->d_order,
                   c->d_queue, c->d_norm_scale, c->d_partials, c->d_bar, c->d_err, c->d_iters,
                   c->d_status, c->d_theta, c->d_adj_g, c->d_adj_u0, c->d_adj_u1,
                   c->d_adj_ls, c->d_adj_gphi, c->d_adj_gmu, c->d_bbpart, c->d_r0, c->d_r1,
@@ -367,7 +367,7 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   int32_t* ip[] = {c->d_ci, c->d_cj, c->d_cperm, c->d_dlist, c->d_split_cs, c->d_split_own};
   for (auto p : ip) if (p) cudaFree(p);
   void* vp[] = {c->d_cR, c->d_cmu, c->d_cphi, c->d_comega, c->d_cmu2, c->d_lam, c->d_lam_star,
-                c->d_dstar};
+                c->d_lam2, c->d_lam_star2, c->d_dstar};
   for (auto p : vp) if (p) cudaFree(p);
   VFPI_TRY_CUDA(dalloc(&c->d_ci, 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_cj, 4 * (size_t)n_c));
@@ -382,6 +382,8 @@ vfpi_status set_contacts(vfpi_ctx* c, const vfpi_contacts* J) {
   VFPI_TRY_CUDA(dalloc(&c->d_cmu2, c->esz * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam, c->esz * 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_lam_star, c->esz * 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_lam2, c->esz * 4 * (size_t)n_c));
+  VFPI_TRY_CUDA(dalloc(&c->d_lam_star2, c->esz * 4 * (size_t)n_c));
   VFPI_TRY_CUDA(dalloc(&c->d_dstar, c->esz * 8 * (size_t)n_c));
   cudaStream_t st = c->stream;
   VFPI_TRY_CUDA(cudaMemcpyAsync(c->d_ci, c->h_ci.data(), 4 * (size_t)n_c, cudaMemcpyHostToDevice, st));
@@ -903,7 +905,7 @@ vfpi_status vfpi_create(const vfpi_bsr* A, const void* b, const vfpi_contacts* J
   CREATE_ST(ensure_vals6(c));
   if (o->grid_ctas < 0) { c->err = "grid_ctas must be >= 0"; return fail(VFPI_ERR_INVALID_ARG); }
   CREATE_CUDA(DISPATCH(c, configure(c)));
-  CREATE_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)std::max(c->max_grid, 1)));
+  CREATE_CUDA(dalloc(&c->d_partials, 8 * 3 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(dalloc(&c->d_items, 8 * (size_t)std::max(c->max_grid, 1)));
   CREATE_CUDA(cudaStreamSynchronize(st));
@@ -1452,7 +1454,7 @@ vfpi_status vfpi_configure_launch(vfpi_t c, int32_t kernel_variant, int32_t bloc
     c->d_partials = nullptr;
     c->d_bbpart = nullptr;
     c->d_items = nullptr;
-    VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 2 * (size_t)c->max_grid));
+    VFPI_TRY_CUDA(dalloc(&c->d_partials, 8 * 3 * (size_t)c->max_grid));
     VFPI_TRY_CUDA(dalloc(&c->d_bbpart, 8 * 6 * (size_t)c->max_grid));
     VFPI_TRY_CUDA(dalloc(&c->d_items, 8 * (size_t)c->max_grid));
   }

@@ -69,6 +69,8 @@ struct DevProblem {
   int aniso;                     // elliptic friction cones (strict operator, Prop. 6)
   Vec4<T>* lam;                  // [n_c] lambda of the last sweep (n, t1, t2)
   Vec4<T>* lam_star;             // [n_c] lambda* of the last sweep
+  Vec4<T>* lam2;                 // [n_c] the same for odd sweeps under the lagged stop
+  Vec4<T>* lam_star2;            //   test (copied to lam / lam_star at the end)
   const Vec4<T>* adj_ls;         // adjoint: frozen lambda* defining the active set
   T* adj_gphi;                   // adjoint: dL/dphi [n_c] (internal order)
   T* adj_gmu;                    // adjoint: dL/dmu  [n_c]
@@ -98,7 +100,8 @@ struct SolveCtl {
   int32_t l_max;
   double theta_th;
   const double* norm_scale;      // [n_scenes] 1 or 1/sqrt(n_q)
-  double* partials;              // [2][grid] FP64 block partials (grid path)
+  double* partials;              // [3][grid] FP64 block partials (grid path; 2 used
+                                 //   unless lag_stop)
   unsigned int* bar;             // [1] barrier arrivals, zeroed per launch (grid path)
   int32_t n_scenes;
   const int32_t* order;          // [n_scenes] processing order (largest first)
@@ -129,6 +132,9 @@ struct SolveCtl {
   int32_t l0;
   double nu0;
   int32_t swap_end;
+  // TMA ring kernel: the stop test of sweep l runs while the barrier of sweep
+  // l + 1 completes (the sweep after a stop is discarded; same iterates)
+  int32_t lag_stop;
 };
 
 
@@ -148,6 +154,7 @@ struct ChebStep {
   int on;       // Alg. 3 active
   int accel;    // l >= l_s: nu from the Chebyshev recurrence (else nu = 1)
   T nu, u;
+  int lam_alt = 0;   // lagged stop test: this sweep's lambda goes to lam2 / lam_star2
 };
 
 // nu_{l+1} of Alg. 3 from the slow-start index, the estimate rho and nu_l.
@@ -735,8 +742,8 @@ __device__ __forceinline__ double finish_row_core(const DevProblem<T>& P, int ro
       vn.x += ww.x * dx;                               // eq. (vup)
       vn.y += ww.x * dy;
       vn.z += ww.x * dz;
-      stv(P.lam + cs, lam);
-      stv(P.lam_star + cs, ls);
+      stv((ch.lam_alt ? P.lam2 : P.lam) + cs, lam);
+      stv((ch.lam_alt ? P.lam_star2 : P.lam_star) + cs, ls);
     }
   }
   vn = cheb_combine(ch, vn, vo, out);   // *out holds v^{l-1} (u^{l-1} in the adjoint)
@@ -1033,6 +1040,75 @@ __device__ __forceinline__ bool sweep_sum_barrier(double acc, double* part, unsi
   return *s_ok != 0;
 }
 
+// The same end of sweep with the stop test one sweep behind: warp 0 publishes
+// the CTA's partial of this sweep and arrives, then -- while the other CTAs
+// arrive -- adds the previous sweep's partials (complete since the last
+// barrier; `prev` null on the first sweep) in the same fixed order, and only
+// then waits.  *total / *theta are the previous sweep's.  Three rotating
+// slices of partials: a CTA still adding sweep l - 1's while a faster one
+// publishes sweep l + 1's reads another slice.
+template <int NT>
+__device__ __forceinline__ bool sweep_sum_barrier_lag(double acc, double* part, const double* prev,
+                                                      unsigned int* bar, unsigned int& nb,
+                                                      double* red, int* s_ok, double nscale,
+                                                      double* total, double* theta) {
+  __shared__ double stage[NT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  stage[threadIdx.x] = acc;
+  __syncthreads();   // every row of this sweep written, every thread's partial staged
+  nb += gridDim.x;
+  if (wid == 0) {
+    double y = stage[lane];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) y += stage[w * 32 + lane];
+    y = warp_sum(y);
+    if (lane == 0) {
+      part[blockIdx.x] = y;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    }
+    double s2w = 0.0;
+    if (prev) {
+      for (int q = lane; q < (int)gridDim.x; q += 32) s2w += prev[q];
+      s2w = warp_sum(s2w);
+    }
+    int ok = 0;
+    if (lane == 0) {
+      for (long long it = 0; it < kBarrierPolls; ++it) {
+        if (ld_acquire_gpu(bar) >= nb) { ok = 1; break; }
+        if (it > 64) __nanosleep(32);
+      }
+      red[32] = s2w;
+      red[33] = sqrt(s2w) * nscale;
+      *s_ok = ok;
+    }
+  }
+  __syncthreads();
+  *total = red[32];
+  *theta = red[33];
+  return *s_ok != 0;
+}
+
+// Fixed-order sum of a completed sweep's CTA partials (as at the end of
+// sweep_sum_barrier) and its theta, for every thread of the CTA.
+template <int NT>
+__device__ __forceinline__ void grid_partials_theta(const double* part, double* red, double nscale,
+                                                    double* total, double* theta) {
+  __syncthreads();   // every thread has read the last values handed out in red
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
+    double s2w = 0.0;
+    for (int q = lane; q < (int)gridDim.x; q += 32) s2w += part[q];
+    s2w = warp_sum(s2w);
+    if (lane == 0) {
+      red[32] = s2w;
+      red[33] = sqrt(s2w) * nscale;
+    }
+  }
+  __syncthreads();
+  *total = red[32];
+  *theta = red[33];
+}
+
 // End of a grid launch whose last sweep left the latest iterate in v1: each
 // warp's rows into v0, or, for a shard (swap_end), the two buffers trade
 // places -- v0 the latest, v1 the one before, which Alg. 3 reads next launch
@@ -1322,6 +1398,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     if (tma_issue_wrap(P, pc, gw, nw, lane, ring + (size_t)(issued % NST) * G::kStage,
                        bars + issued % NST))
       ++issued;
+  const bool lag = ctl.lag_stop != 0;
   for (;; ++l) {
     const Vec4<T>* vin = cur ? P.v1 : P.v0;
     Vec4<T>* vout = cur ? P.v0 : P.v1;
@@ -1331,6 +1408,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     ch.accel = ch.on && lg >= ctl.cheb_ls;
     ch.nu = (T)nu;
     ch.u = (T)ctl.cheb_u;
+    ch.lam_alt = lag ? (l & 1) : 0;
     double acc = 0.0;
     for (int s = gw; s < P.n_slices && !failed; s += nw) {
       const int len = P.slice_len[s];
@@ -1416,6 +1494,32 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
       for (int d = blockIdx.x * NT + threadIdx.x; d < ctl.n_d; d += gridDim.x * NT)
         acc += d_contact<T, ADJ>(P, P.d_list[d], vin, vout, ch);
     }
+    if (lag) {
+      // stop test of sweep l - 1 (its v is this sweep's input, still intact;
+      // its lambda in the other buffers): a stop discards this sweep
+      double s2p = 0.0, thp = 0.0;
+      if (!sweep_sum_barrier_lag<NT>(acc, ctl.partials + (l % 3) * gridDim.x,
+                                     l > 1 ? ctl.partials + ((l - 1) % 3) * gridDim.x : nullptr,
+                                     ctl.bar, nbar, red, &s_ok, nscale, &s2p, &thp)) {
+        st = ST_TIMEOUT;
+        break;
+      }
+      if (l > 1 && (!isfinite(thp) || thp < ctl.theta_th)) {
+        st = isfinite(thp) ? ST_OK : ST_NONFINITE;
+        theta = thp;
+        s2 = s2p;
+        --l;
+        break;
+      }
+      if (l >= ctl.l_max) {   // the last sweep allowed: its own test, its barrier passed
+        grid_partials_theta<NT>(ctl.partials + (l % 3) * gridDim.x, red, nscale, &s2, &theta);
+        cur ^= 1;
+        st = !isfinite(theta) ? ST_NONFINITE : theta < ctl.theta_th ? ST_OK : ST_NOT_CONVERGED;
+        break;
+      }
+      cur ^= 1;
+      continue;
+    }
     if (!sweep_sum_barrier<NT>(acc, ctl.partials + (l & 1) * gridDim.x, ctl.bar, nbar, red, &s_ok,
                                nscale, cs, lg, ctl.cheb_ls, &s2, &theta, &nu)) {
       st = ST_TIMEOUT;
@@ -1435,6 +1539,13 @@ __global__ void __launch_bounds__(NT, 1) k_solve_grid_tma(DevProblem<T> P, Solve
     ++consumed;
   }
   if (st != ST_TIMEOUT && cur == 1) end_of_grid_launch(P, ctl, gw, nw, lane);
+  // lagged stop test: an odd last sweep left its lambda in the second buffers
+  // (every CTA is past that sweep's barrier and the next sweep's, if any)
+  if (lag && st != ST_TIMEOUT && (l & 1))
+    for (int q = blockIdx.x * NT + threadIdx.x; q < P.n_c; q += gridDim.x * NT) {
+      stv(P.lam + q, ldv(P.lam2 + q));
+      stv(P.lam_star + q, ldv(P.lam_star2 + q));
+    }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl.iters[0] = l;
     ctl.theta[0] = theta;

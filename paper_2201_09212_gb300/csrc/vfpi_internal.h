@@ -112,10 +112,11 @@ struct vfpi_ctx {
   void* d_cmu2 = nullptr;                   // friction along t2 (elliptic cones)
   int aniso = 0;
   void *d_lam = nullptr, *d_lam_star = nullptr;
+  void *d_lam2 = nullptr, *d_lam_star2 = nullptr;   // odd sweeps' lambda under the lagged stop test
   void* d_dstar = nullptr;                  // D-contact v* staging [2 n_c]
   int32_t *d_scene_slice = nullptr, *d_scene_d = nullptr, *d_order = nullptr, *d_queue = nullptr;
   double* d_norm_scale = nullptr;
-  double* d_partials = nullptr;
+  double* d_partials = nullptr;   // [3][max_grid]
   double* d_sumsq = nullptr;                // the grid kernels' last sum ||dv||^2
   double* d_bbpart = nullptr;               // BB dot-product partials [2][max_grid][3]
   void *d_r0 = nullptr, *d_r1 = nullptr;    // BB residual ping-pong (allocated on use)

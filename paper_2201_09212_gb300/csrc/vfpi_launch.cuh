@@ -45,6 +45,8 @@ DevProblem<T> dev_problem(vfpi_ctx* c, bool adjoint = false) {
   P.prox = c->opts.operator_ == VFPI_OP_PROXIMAL ? 1 : 0;
   P.lam = static_cast<Vec4<T>*>(c->d_lam);
   P.lam_star = static_cast<Vec4<T>*>(c->d_lam_star);
+  P.lam2 = static_cast<Vec4<T>*>(c->d_lam2);
+  P.lam_star2 = static_cast<Vec4<T>*>(c->d_lam_star2);
   P.d_list = c->d_dlist;
   P.dstar = static_cast<Vec4<T>*>(c->d_dstar);
   P.v0 = static_cast<Vec4<T>*>(c->d_v0);
@@ -539,6 +541,11 @@ cudaError_t Launch<T>::solve(vfpi_ctx* c, int l_max, double theta_th, bool adjoi
   ctl.l0 = shard ? c->shard_l : 1;
   ctl.nu0 = shard ? c->shard_cheb.nu : 1.0;
   ctl.swap_end = shard ? 1 : 0;
+  // the TMA ring kernel's lagged stop test: forward Alg. 1 sweeps (no
+  // Chebyshev weight, which needs the last theta before the next sweep), no
+  // D-contacts (their second barrier), more than one sweep
+  ctl.lag_stop = (c->path == 1 && c->tma_stages > 0 && !adjoint && !c->bb_rule && !shard &&
+                  ctl.cheb_ls <= 0 && c->n_d == 0 && l_max > 1) ? 1 : 0;
   if (ctl.theta_rel && c->path == 1 && c->n_slices > 0) {   // (the per-scene kernels compute theirs)
     k_slice_sumsq<T><<<blocks_for((int64_t)c->n_slices * 32, 256), 256, 0, s>>>(
         c->n_slices, static_cast<const Vec4<T>*>(c->d_adj_g), c->d_slicesq);
