@@ -46,13 +46,13 @@ ADJ_CHEBYSHEV = (5, 1.0)    # Alg. 3 on the adjoint iteration (slow start, under
 # kernel, keyed by (hash of the CUDA sources it was captured from, kernel
 # variant), each captured at the variant's default CTA count; stale entries
 # read as null (the grid kernel's ncu summary gives the captures)
-NCU_TRAFFIC = {("3b32b1a118c1cf0d", 0): 554553768, ("3b32b1a118c1cf0d", 7): 553416634,
-               ("3b32b1a118c1cf0d", 28): 388319106, ("3b32b1a118c1cf0d", 29): 387834361}
+NCU_TRAFFIC = {("0d1008fea7fe258c", 0): 554637560, ("0d1008fea7fe258c", 7): 553524952,
+               ("0d1008fea7fe258c", 28): 388417174, ("0d1008fea7fe258c", 29): 387921396}
 # the same for the batched kernel: (DRAM read + write bytes, algorithmic bytes)
 # of one captured env-step solve launch (the bench's launch log gives the
 # captured launch's own count), keyed by (source hash, storage of A as
 # Solver.storage() names it, threads per CTA)
-NCU_BATCH_TRAFFIC = {("3b32b1a118c1cf0d", "blocks6", 256): (114014633800, 172972435132)}
+NCU_BATCH_TRAFFIC = {("0d1008fea7fe258c", "blocks6", 256): (114027696568, 172972435132)}
 # kernel-name notes for the compressed storages of A (the fraction keeps the
 # 40-byte full-BSR count per block, so on these it is an effective one)
 STORAGE_NOTE = {
