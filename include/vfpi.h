@@ -330,7 +330,8 @@ vfpi_status vfpi_last_kernel_ms(vfpi_t ctx, float* ms);
 vfpi_status vfpi_get_layout(vfpi_t ctx, int64_t* info8);
 
 /* How the solve kernels read A (no work on the device): info4[0] the storage
- * of the forward sweep in the current launch shape -- 0 the full 3x3 blocks
+ * of the forward Alg. 1 sweep in the current launch shape (Barzilai-Borwein
+ * sweeps always read the full blocks) -- 0 the full 3x3 blocks
  * (36 + 4 bytes per block), 1 the symmetric storage (upper blocks, grid
  * path), 2 the symmetric-block storage (6 values per block, 24 + 4 bytes);
  * [1] every stored block is symmetric bit for bit; [2] A is symmetric (grid

@@ -544,9 +544,10 @@ class Solver:
     STORAGE_NAMES = ("full", "symmetric", "blocks6")
 
     def storage(self) -> dict:
-        """How the solve kernels read A: the forward sweep's storage in the
-        current launch shape (``full``, ``symmetric`` or ``blocks6``) and the
-        flags that allow the others."""
+        """How the solve kernels read A: the forward Alg. 1 sweep's storage in
+        the current launch shape (``full``, ``symmetric`` or ``blocks6``;
+        Barzilai-Borwein sweeps read ``full``) and the flags that allow the
+        others."""
         info = (C.c_int32 * 4)()
         self._check(self._L.vfpi_get_storage(self._h, info))
         return {"storage": self.STORAGE_NAMES[int(info[0])], "blocks_symmetric": bool(info[1]),
