@@ -191,7 +191,11 @@ enum {
   /* Grid path again: the TMA ring with two stages per warp (threads per CTA /
    * stages): half the shared memory per warp of VFPI_VARIANT_TMA_256_4, so
    * twice the warps fit -- for mid-size scenes whose sweeps are bounded by
-   * each warp's chain of dependent loads rather than by bandwidth. */
+   * each warp's chain of dependent loads rather than by bandwidth.  The ring
+   * kernels (8-11, 26, 27) take a forward Alg. 1 solve's stop test one sweep
+   * behind, while the next sweep's grid barrier completes, and discard that
+   * sweep on a stop (not with Alg. 3 or D-contacts): v, lambda, the
+   * iteration count and theta are those of the other kernels. */
   VFPI_VARIANT_TMA_256_2 = 26,
   VFPI_VARIANT_TMA_128_2 = 27,
   /* Symmetric-block storage, when every 3x3 block of A equals its transpose
