@@ -302,9 +302,17 @@ def solve(engine, plan: ShardPlan, comm: TorchComm, v0_own, *, n_dof: int, theta
     _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
                                           recv_shapes, dtype))
 
+    empty = torch.empty(0, dtype=dtype, device=device)
+
     def sweep():
         if not n_split:
-            return engine.shard_sweep()
+            # the next sweep's halo rows go out behind this sweep on the stream,
+            # before its sum is waited for (an exchange after the last sweep is
+            # harmless: it writes halo rows only)
+            engine.shard_sweep(sumsq=False)
+            _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
+                                                  recv_shapes, dtype))
+            return engine.finish_split(empty)
         engine.shard_sweep(sumsq=False)
         vs = engine.split_vstar(out=torch.empty(3 * n_split, dtype=dtype, device=device))
         got = comm.exchange(_split_sends(plan, vs, 3), _split_shapes(plan, 3), dtype)
@@ -323,8 +331,9 @@ def solve(engine, plan: ShardPlan, comm: TorchComm, v0_own, *, n_dof: int, theta
         if l == l_max:
             break
         engine.shard_set_theta(theta)
-        _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
-                                              recv_shapes, dtype))
+        if n_split:   # (split contacts finish their rows after the v* exchange)
+            _set_halo(engine, plan, comm.exchange(_sends(engine, plan, torch, dtype, device),
+                                                  recv_shapes, dtype))
     return ShardResult(engine.get_velocity(), l, theta, status)
 
 
@@ -373,6 +382,7 @@ def solve_local(engines, plans, v0, *, n_dof: int, theta_th: float, l_max: int,
             parts = [e.finish_split(x if x is not None else empty)
                      for e, x in zip(engines, split_exchange(vs, 3))]
         else:
+            exchange()     # queued behind the sweeps, before their sums are waited for
             parts = [e.finish_split(empty) for e in engines]
         s2 = 0.0
         for x in parts:
@@ -387,6 +397,7 @@ def solve_local(engines, plans, v0, *, n_dof: int, theta_th: float, l_max: int,
             break
         for e in engines:
             e.shard_set_theta(theta)
-        exchange()
+        if split:
+            exchange()
     v = np.concatenate([np.asarray(e.get_velocity()) for e in engines])
     return ShardResult(v, l, theta, status)
